@@ -1,0 +1,58 @@
+// kernels.h -- declarations of the sdpgpu device kernels and job records.
+#pragma once
+#include "common.cuh"
+
+namespace sdpg {
+
+enum { EPI_STORE = 0, EPI_PARTIAL = 1, EPI_RECON_POS = 2, EPI_RECON_NEG = 3 };
+
+// One product of a batched GEMM launch (see k_gemm).
+struct GemmJob {
+  const double* A;
+  const double* B;
+  double* C;
+  const double* colscale;  // optional scale of op(A)'s columns (the k index)
+  const double* Eb;        // reconstruction: W
+  double* C2;              // reconstruction: Y; Gram reduce: destination
+  int lda, ldb, ldc;
+  int M, N, K;
+  int splits, tiles_m, tiles_n, epi;
+  double alpha, beta, rho;
+};
+
+// admm_kernels.cu
+__global__ void k_admm_sparse_r(Inst* insts, WorkMap wm);
+__global__ void k_admm_cons_u(Inst* insts, WorkMap wm);
+__global__ void k_admm_ksolve(Inst* insts, const int* list);
+__global__ void k_admm_sparse_corr(Inst* insts, WorkMap wm);
+__global__ void k_admm_dense(Inst* insts, WorkMap wm);
+__global__ void k_admm_sparse_fix(Inst* insts, WorkMap wm);
+__global__ void k_check_dense(Inst* insts, WorkMap wm);
+__global__ void k_check_sparse(Inst* insts, WorkMap wm);
+__global__ void k_check_cons(Inst* insts, WorkMap wm);
+__global__ void k_cone_fill(Inst* insts, WorkMap wm, const double* scale, int which, double shift);
+__global__ void k_cone_chol(Inst* insts, const int* list);
+
+// lobpcg_kernels.cu
+template <bool TA, bool TB, typename TC>
+__global__ void k_gemm(const GemmJob* jobs, WorkMap wm);
+__global__ void k_gram_reduce(const GemmJob* jobs, WorkMap wm, int symmetrize);
+template <typename T>
+__global__ void k_rayleigh_ritz(Inst* insts, const int* list);
+__global__ void k_resid(Inst* insts, WorkMap wm);
+__global__ void k_resid_finish(Inst* insts, const int* list, int last_allowed);
+__global__ void k_compact(Inst* insts, WorkMap wm);
+__global__ void k_fill_random(Inst* insts, WorkMap wm, const int* col0, const int* ncols, const int* draw,
+                              const unsigned* stream, unsigned long long seed);
+
+// jacobi_kernels.cu (exact branch)
+__global__ void k_jac_init(Inst* insts, WorkMap wm, int negate);
+__global__ void k_jac_angles(Inst* insts, WorkMap wm, int round);
+__global__ void k_jac_apply(Inst* insts, WorkMap wm, int round);
+__global__ void k_jac_sort(Inst* insts, const int* list);
+__global__ void k_jac_gather(Inst* insts, WorkMap wm);
+__global__ void k_fro2(Inst* insts, WorkMap wm);
+__global__ void k_seed_block(Inst* insts, WorkMap wm);
+__global__ void k_copy_cols(const double* src, int lds, double* dst, int ldd, int rows, int cols, double scale);
+
+}  // namespace sdpg

@@ -1,0 +1,495 @@
+// lobpcg_kernels.cu -- CUDA-core kernels of the projection onto the PSD cone:
+// batched block products (W times a block, Gram matrices, block updates and
+// the rank-k reconstruction of Eq. 2), the per-instance Rayleigh-Ritz step
+// (Algorithm 2: Cholesky QR + symmetric eigendecomposition by parallel
+// cyclic Jacobi) and the residual/normalisation kernels of Algorithm 3.
+//
+// Products run in `TC` arithmetic (double for the FP64 path, float for the
+// mixed path's Grams and updates); storage is FP64 throughout.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace sdpg {
+
+// ---------------------------------------------------------------------------
+// Batched tiled GEMM: C = alpha op(A) op(B) (+ beta C), 64x64 tiles, k-step
+// 16, 256 threads with a 4x4 register tile each.  op(A) is M x K, op(B) is
+// K x N; TA: A stored K x M (column-major), TB: B stored N x K.
+// Job `j` covers tiles_m * tiles_n * splits CTAs; split s handles a K-range
+// and (EPI_PARTIAL) writes its own partial matrix at C + s*ldc*N.
+// ---------------------------------------------------------------------------
+template <bool TA, bool TB, typename TC>
+__global__ void __launch_bounds__(256) k_gemm(const GemmJob* jobs, WorkMap wm) {
+  __shared__ TC As[16][65];
+  __shared__ TC Bs[16][65];
+  int local;
+  const int ji = find_inst(wm, blockIdx.x, &local);
+  const GemmJob J = jobs[ji];
+  const int tiles_mn = J.tiles_m * J.tiles_n;
+  const int split = local / tiles_mn;
+  const int t = local - split * tiles_mn;
+  const int r0 = (t % J.tiles_m) * 64, c0 = (t / J.tiles_m) * 64;
+  int kchunk = (J.K + J.splits - 1) / J.splits;
+  kchunk = (kchunk + 15) & ~15;
+  const int k0 = split * kchunk;
+  const int k1 = min(J.K, k0 + kchunk);
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  TC acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = (TC)0;
+  for (int kk = k0; kk < k1; kk += 16) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      int lin = tid + e * 256, i, k;
+      if (!TA) { i = lin & 63; k = lin >> 6; }
+      else { k = lin & 15; i = lin >> 4; }
+      int gi = r0 + i, gk = kk + k;
+      TC val = (TC)0;
+      if (gi < J.M && gk < k1) {
+        double a = TA ? J.A[(size_t)gk + (size_t)gi * J.lda] : J.A[(size_t)gi + (size_t)gk * J.lda];
+        if (J.colscale) a *= J.colscale[gk];
+        val = (TC)a;
+      }
+      As[k][i] = val;
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      int lin = tid + e * 256, j, k;
+      if (!TB) { k = lin & 15; j = lin >> 4; }
+      else { j = lin & 63; k = lin >> 6; }
+      int gj = c0 + j, gk = kk + k;
+      TC val = (TC)0;
+      if (gj < J.N && gk < k1)
+        val = (TC)(TB ? J.B[(size_t)gj + (size_t)gk * J.ldb] : J.B[(size_t)gk + (size_t)gj * J.ldb]);
+      Bs[k][j] = val;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      TC a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { a[q] = As[k][tx + 16 * q]; b[q] = Bs[k][ty + 16 * q]; }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[q][r] += a[q] * b[r];
+    }
+    __syncthreads();
+  }
+  // epilogue: thread (tx, ty) owns rows r0 + tx + 16q, cols c0 + ty + 16r
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    int j = c0 + ty + 16 * r;
+    if (j >= J.N) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int i = r0 + tx + 16 * q;
+      if (i >= J.M) continue;
+      double v = (double)acc[q][r];
+      size_t o = (size_t)i + (size_t)j * J.ldc;
+      if (J.epi == EPI_PARTIAL) {
+        J.C[o + (size_t)split * J.ldc * J.N] = v;
+      } else if (J.epi == EPI_STORE) {
+        J.C[o] = J.beta == 0.0 ? J.alpha * v : J.alpha * v + J.beta * J.C[o];
+      } else {  // EPI_RECON_POS / EPI_RECON_NEG: Z = [W] + acc, Y = rho (W - Z)
+        double w = J.Eb[o];
+        double z = (J.epi == EPI_RECON_NEG ? w : 0.0) + v;
+        J.C[o] = z;
+        J.C2[o] = J.rho * (w - z);
+      }
+    }
+  }
+}
+
+// Sum the split-K partials of a Gram job; optionally symmetrise.
+__global__ void k_gram_reduce(const GemmJob* jobs, WorkMap wm, int symmetrize) {
+  int local;
+  const int ji = find_inst(wm, blockIdx.x, &local);
+  const GemmJob J = jobs[ji];
+  int e = local * blockDim.x + threadIdx.x;
+  if (e >= J.M * J.N) return;
+  int i = e % J.M, j = e / J.M;
+  double s = 0.0, st = 0.0;
+  size_t stride = (size_t)J.ldc * J.N;
+  for (int k = 0; k < J.splits; ++k) {
+    s += J.C[(size_t)i + (size_t)j * J.ldc + k * stride];
+    if (symmetrize) st += J.C[(size_t)j + (size_t)i * J.ldc + k * stride];
+  }
+  J.C2[(size_t)i + (size_t)j * J.M] = symmetrize ? 0.5 * (s + st) : s;
+}
+
+// ---------------------------------------------------------------------------
+// Rayleigh-Ritz (Algorithm 2) on a trial subspace S of width p, given its
+// Gram matrix G = S^T S and M = S^T A S (p x p, leading dimension p):
+//   L = chol(G), Linv = L^{-1}, H = Linv M Linv^T, (Theta, U) = eig(H)
+//   ascending, Coef = Linv^T U[:, top keep]; the Ritz vectors are S Coef.
+// This is Rayleigh-Ritz with Cholesky-QR orthonormalisation (Q = S L^{-T})
+// written without forming Q.  One CTA per instance; T is the arithmetic.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct RRConst;
+template <>
+struct RRConst<double> {
+  static constexpr double jac_eps = 4e-16;
+  static constexpr double piv_min = 1e-12;
+  static constexpr int max_sweeps = 40;
+};
+template <>
+struct RRConst<float> {
+  static constexpr double jac_eps = 4e-7;
+  static constexpr double piv_min = 1e-6;
+  static constexpr int max_sweeps = 25;
+};
+
+// round-robin (circle method) pairing for np (even) indices, round r, pair k
+__device__ __forceinline__ void rr_pair(int r, int k, int np, int* a, int* b) {
+  if (k == 0) {
+    *a = 0;
+    *b = 1 + (r % (np - 1));
+  } else {
+    *a = 1 + (r + k) % (np - 1);
+    *b = 1 + (r - k + (np - 1)) % (np - 1);
+  }
+}
+
+// CTA-wide cyclic Jacobi (parallel ordering) on symmetric H (p x p, ld ldh),
+// accumulating the rotations into U (set to I here).  Returns sweeps.
+template <typename T>
+__device__ int cta_jacobi(int p, double* H, int ldh, double* U, int ldu, double* shc, double* shs, int* sha,
+                          int* shb, double* red) {
+  const int np = p + (p & 1), P2 = np / 2;
+  for (int t = threadIdx.x; t < p * p; t += blockDim.x) U[idx2(t % p, t / p, ldu)] = (t % p == t / p) ? 1.0 : 0.0;
+  // ||H||_F
+  double part = 0.0;
+  for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
+    double h = H[idx2(t % p, t / p, ldh)];
+    part += h * h;
+  }
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+  __syncthreads();
+  __shared__ double thr;
+  __shared__ int rotated;
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    thr = RRConst<T>::jac_eps * sqrt(s) / (double)(p > 0 ? p : 1);
+  }
+  __syncthreads();
+  int sweep = 0;
+  if (p < 2) return 0;
+  for (; sweep < RRConst<T>::max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) rotated = 0;
+    __syncthreads();
+    for (int r = 0; r < np - 1; ++r) {
+      for (int k = threadIdx.x; k < P2; k += blockDim.x) {
+        int a, b;
+        rr_pair(r, k, np, &a, &b);
+        double c = 1.0, s = 0.0;
+        if (a < p && b < p) {
+          T hab = (T)H[idx2(a, b, ldh)];
+          if (fabs((double)hab) > thr) {
+            T haa = (T)H[idx2(a, a, ldh)], hbb = (T)H[idx2(b, b, ldh)];
+            T tau = (hbb - haa) / ((T)2 * hab);
+            T tt = (tau >= (T)0 ? (T)1 : (T)-1) / (fabs(tau) + sqrt((T)1 + tau * tau));
+            T cc = (T)1 / sqrt((T)1 + tt * tt);
+            c = (double)cc;
+            s = (double)(tt * cc);
+            rotated = 1;
+          }
+        }
+        shc[k] = c; shs[k] = s; sha[k] = a; shb[k] = b;
+      }
+      __syncthreads();
+      // two-sided update of every 2x2 block (pair i rows, pair j cols)
+      for (int e = threadIdx.x; e < P2 * P2; e += blockDim.x) {
+        int ki = e % P2, kj = e / P2;
+        int ai = sha[ki], bi = shb[ki], aj = sha[kj], bj = shb[kj];
+        T ci = (T)shc[ki], si = (T)shs[ki], cj = (T)shc[kj], sj = (T)shs[kj];
+        bool vai = ai < p, vbi = bi < p, vaj = aj < p, vbj = bj < p;
+        T haa = (vai && vaj) ? (T)H[idx2(ai, aj, ldh)] : (T)0;
+        T hab = (vai && vbj) ? (T)H[idx2(ai, bj, ldh)] : (T)0;
+        T hba = (vbi && vaj) ? (T)H[idx2(bi, aj, ldh)] : (T)0;
+        T hbb = (vbi && vbj) ? (T)H[idx2(bi, bj, ldh)] : (T)0;
+        T taa = cj * haa - sj * hab, tab = sj * haa + cj * hab;
+        T tba = cj * hba - sj * hbb, tbb = sj * hba + cj * hbb;
+        T naa = ci * taa - si * tba, nba = si * taa + ci * tba;
+        T nab = ci * tab - si * tbb, nbb = si * tab + ci * tbb;
+        if (ki == kj && si != (T)0) { nab = (T)0; nba = (T)0; }
+        if (vai && vaj) H[idx2(ai, aj, ldh)] = (double)naa;
+        if (vai && vbj) H[idx2(ai, bj, ldh)] = (double)nab;
+        if (vbi && vaj) H[idx2(bi, aj, ldh)] = (double)nba;
+        if (vbi && vbj) H[idx2(bi, bj, ldh)] = (double)nbb;
+      }
+      for (int e = threadIdx.x; e < p * P2; e += blockDim.x) {
+        int row = e % p, k = e / p;
+        int a = sha[k], b = shb[k];
+        if (a >= p || b >= p || shs[k] == 0.0) continue;
+        T c = (T)shc[k], s = (T)shs[k];
+        T ua = (T)U[idx2(row, a, ldu)], ub = (T)U[idx2(row, b, ldu)];
+        U[idx2(row, a, ldu)] = (double)(c * ua - s * ub);
+        U[idx2(row, b, ldu)] = (double)(s * ua + c * ub);
+      }
+      __syncthreads();
+    }
+    if (!rotated) break;
+    __syncthreads();
+  }
+  return sweep + 1;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_rayleigh_ritz(Inst* insts, const int* list) {
+  const int ii = list[blockIdx.x];
+  const Inst& I = insts[ii];
+  Ctl* ctl = I.ctl;
+  const int p = ctl->p, keep = ctl->keep;
+  double *G = I.G, *M = I.M, *L = I.Linv, *H = I.H, *U = I.U;
+  extern __shared__ double dyn[];
+  double* shc = dyn;
+  double* shs = dyn + (p / 2 + 1);
+  int* sha = (int*)(dyn + 2 * (p / 2 + 1));
+  int* shb = sha + (p / 2 + 1);
+  __shared__ double red[32];
+  __shared__ int fail;
+  if (threadIdx.x == 0) fail = 0;
+  __syncthreads();
+  // 1. Cholesky of G in place (lower triangle), column by column
+  for (int j = 0; j < p; ++j) {
+    if (threadIdx.x == 0) {
+      T d = (T)G[idx2(j, j, p)];
+      if (!(d > (T)RRConst<T>::piv_min)) fail = j + 1;
+      else G[idx2(j, j, p)] = (double)sqrt(d);
+    }
+    __syncthreads();
+    if (fail) break;
+    T ljj = (T)G[idx2(j, j, p)];
+    for (int i = j + 1 + threadIdx.x; i < p; i += blockDim.x) G[idx2(i, j, p)] = (double)((T)G[idx2(i, j, p)] / ljj);
+    __syncthreads();
+    int w = p - j - 1;
+    for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
+      int r = t % w, c = t / w;
+      if (r < c) continue;
+      int i = j + 1 + r, k = j + 1 + c;
+      G[idx2(i, k, p)] = (double)((T)G[idx2(i, k, p)] - (T)G[idx2(i, j, p)] * (T)G[idx2(k, j, p)]);
+    }
+    __syncthreads();
+  }
+  if (fail) {
+    if (threadIdx.x == 0) ctl->rr_fail = fail;
+    return;
+  }
+  // 2. Linv = L^{-1}: one thread per column, forward substitution
+  for (int c = threadIdx.x; c < p; c += blockDim.x) {
+    for (int i = 0; i < c; ++i) L[idx2(i, c, p)] = 0.0;
+    for (int i = c; i < p; ++i) {
+      T acc = (i == c) ? (T)1 : (T)0;
+      for (int k = c; k < i; ++k) acc -= (T)G[idx2(i, k, p)] * (T)L[idx2(k, c, p)];
+      L[idx2(i, c, p)] = (double)(acc / (T)G[idx2(i, i, p)]);
+    }
+  }
+  __syncthreads();
+  // 3. H = Linv M Linv^T  (G reused for T = Linv M)
+  for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
+    int i = t % p, j = t / p;
+    T acc = 0;
+    for (int k = 0; k <= i; ++k) acc += (T)L[idx2(i, k, p)] * (T)M[idx2(k, j, p)];
+    G[idx2(i, j, p)] = (double)acc;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
+    int i = t % p, j = t / p;
+    if (i < j) continue;
+    T acc = 0;
+    for (int k = 0; k <= j; ++k) acc += (T)G[idx2(i, k, p)] * (T)L[idx2(j, k, p)];
+    H[idx2(i, j, p)] = (double)acc;
+    H[idx2(j, i, p)] = (double)acc;
+  }
+  __syncthreads();
+  // 4. eigendecomposition of H
+  int sw = cta_jacobi<T>(p, H, p, U, p, shc, shs, sha, shb, red);
+  __syncthreads();
+  // 5. ascending order of the Ritz values (rank sort); M reused for order
+  int* ord = (int*)M;
+  for (int i = threadIdx.x; i < p; i += blockDim.x) {
+    double li = H[idx2(i, i, p)];
+    int rank = 0;
+    for (int j = 0; j < p; ++j) {
+      double lj = H[idx2(j, j, p)];
+      rank += (lj < li) || (lj == li && j < i);
+    }
+    ord[rank] = i;
+  }
+  __syncthreads();
+  // 6. Coef = Linv^T U[:, top keep], theta = top keep Ritz values
+  for (int t = threadIdx.x; t < p * keep; t += blockDim.x) {
+    int i = t % p, j = t / p;
+    int col = ord[p - keep + j];
+    T acc = 0;
+    for (int k = i; k < p; ++k) acc += (T)L[idx2(k, i, p)] * (T)U[idx2(k, col, p)];
+    I.Coef[idx2(i, j, p)] = (double)acc;
+  }
+  for (int j = threadIdx.x; j < keep; j += blockDim.x) I.theta[j] = H[idx2(ord[p - keep + j], ord[p - keep + j], p)];
+  if (threadIdx.x == 0) {
+    int np = 0;
+    for (int j = 0; j < p; ++j) np += H[idx2(j, j, p)] > 0.0;
+    ctl->npos_rr = np;
+    ctl->rr_fail = 0;
+    ctl->sweeps += sw;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Residuals of Algorithm 3: R = A X - X Theta (fresh columns: Theta = 0)
+// written to the spare buffer S[1-par] at columns [m, 2m); Delta X and
+// A Delta X copied to S[1-par] / AS[1-par] at [2m, 2m+mP); column norms in
+// resn.  grid: (instance, column) over columns [0, m + mP)
+// ---------------------------------------------------------------------------
+__global__ void k_resid(Inst* insts, WorkMap wm) {
+  __shared__ double sh[32];
+  int local;
+  const int ii = find_inst(wm, blockIdx.x, &local);
+  const Inst& I = insts[ii];
+  const Ctl* ctl = I.ctl;
+  const int m = ctl->m, mP = ctl->mP, n = I.n, ld = I.ld;
+  const int j = local;
+  if (j >= m + mP) return;
+  const double* S = I.S[I.par];
+  const double* AS = I.AS[I.par];
+  double* T = I.S[1 - I.par];
+  double* AT = I.AS[1 - I.par];
+  double part = 0.0;
+  if (j < m) {
+    double th = (j < m - ctl->nfresh) ? I.theta[j] : 0.0;
+    const double* x = S + (size_t)j * ld;
+    const double* ax = AS + (size_t)j * ld;
+    double* r = T + (size_t)(m + j) * ld;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      double v = ax[i] - th * x[i];
+      r[i] = v;
+      part += v * v;
+    }
+  } else {
+    size_t off = (size_t)(2 * m + (j - m)) * ld;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      double v = S[off + i];
+      T[off + i] = v;
+      AT[off + i] = AS[off + i];
+      part += v * v;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
+    I.resn[j] = sqrt(s);
+  }
+}
+
+// Per instance: convergence test (every Ritz pair of the block within tol,
+// no fresh columns), residual summaries, and soft locking: only the
+// columns whose residual is above tol (fresh columns always) contribute
+// their R and Delta X to the next trial subspace [X, R_act, dX_act].
+// last_allowed = 0: the step budget is spent, stop.
+__global__ void k_resid_finish(Inst* insts, const int* list, int last_allowed) {
+  const Inst& I = insts[list[blockIdx.x]];
+  Ctl* c = I.ctl;
+  if (threadIdx.x != 0) return;
+  const int m = c->m, mP = c->mP;
+  double rmax = 0.0, rpos2 = 0.0;
+  int npos = 0, ma = 0, mPa = 0;
+  for (int j = 0; j < m; ++j) {
+    double r = I.resn[j];
+    bool fresh = j >= m - c->nfresh;
+    rmax = fmax(rmax, r);
+    if (!fresh && I.theta[j] > 0.0) {
+      ++npos;
+      rpos2 += r * r;
+    }
+    bool act = fresh || r > c->tol;
+    I.slot[j] = act && r > 0.0 ? ma++ : -1;
+  }
+  for (int j = 0; j < mP; ++j)
+    if (I.slot[j] >= 0 && I.resn[m + j] > 0.0) ++mPa;
+  c->res_max = rmax;
+  c->res_pos2 = rpos2;
+  c->npos = npos;
+  c->ma = ma;
+  c->mPa = mPa;
+  bool conv = (c->nfresh == 0) && (rmax <= c->tol);
+  if (conv || !last_allowed || ma == 0) c->active = 0;
+  c->p = m + ma + mPa;
+  c->keep = m;
+}
+
+// Compact the active residual and Delta X columns into S[par] after X,
+// scaled to unit norm (the trial subspace is unchanged by column scaling;
+// Cholesky QR sees a well-scaled Gram matrix).  Reads only the spare
+// buffers written by k_resid.  grid: (instance, column) over [0, m + mP).
+__global__ void k_compact(Inst* insts, WorkMap wm) {
+  int local;
+  const int ii = find_inst(wm, blockIdx.x, &local);
+  const Inst& I = insts[ii];
+  const Ctl* ctl = I.ctl;
+  const int m = ctl->m, mP = ctl->mP, ma = ctl->ma;
+  const int j = local;
+  if (!ctl->active || j >= m + mP) return;
+  const int jj = j < m ? j : j - m;
+  int sl = I.slot[jj];
+  if (sl < 0) return;
+  double* S = I.S[I.par];
+  double* AS = I.AS[I.par];
+  const double* T = I.S[1 - I.par];
+  const double* AT = I.AS[1 - I.par];
+  if (j < m) {
+    double sc = 1.0 / I.resn[j];
+    const double* src = T + (size_t)(m + j) * I.ld;
+    double* dst = S + (size_t)(m + sl) * I.ld;
+    for (int i = threadIdx.x; i < I.n; i += blockDim.x) dst[i] = sc * src[i];
+  } else {
+    double nr = I.resn[m + jj];
+    if (!(nr > 0.0)) return;
+    // rank of this Delta X column among the active ones
+    int r = 0;
+    for (int q = 0; q < jj; ++q) r += (I.slot[q] >= 0 && I.resn[m + q] > 0.0);
+    double sc = 1.0 / nr;
+    size_t so = (size_t)(2 * m + jj) * I.ld, dof = (size_t)(m + ma + r) * I.ld;
+    for (int i = threadIdx.x; i < I.n; i += blockDim.x) {
+      S[dof + i] = sc * T[so + i];
+      AS[dof + i] = sc * AT[so + i];
+    }
+  }
+}
+
+// Fresh Gaussian columns of the expansion (Algorithm 3, last line), from
+// the same Philox stream as the oracle: (row, col, draw, stream) with
+// draw = expansion count and stream = ADMM iteration.
+__global__ void k_fill_random(Inst* insts, WorkMap wm, const int* col0, const int* ncols, const int* draw,
+                              const unsigned* stream, unsigned long long seed) {
+  int local;
+  const int ii = find_inst(wm, blockIdx.x, &local);
+  const Inst& I = insts[ii];
+  const int j = local;
+  if (j >= ncols[ii]) return;
+  double* S = I.S[I.par];
+  double* dst = S + (size_t)(col0[ii] + j) * I.ld;
+  for (int i = threadIdx.x; i < I.n; i += blockDim.x)
+    dst[i] = philox_normal(seed, stream[ii], (uint32_t)draw[ii], (uint32_t)i, (uint32_t)j);
+}
+
+// Explicit instantiations
+template __global__ void k_gemm<false, false, double>(const GemmJob*, WorkMap);
+template __global__ void k_gemm<true, false, double>(const GemmJob*, WorkMap);
+template __global__ void k_gemm<false, true, double>(const GemmJob*, WorkMap);
+template __global__ void k_gemm<false, false, float>(const GemmJob*, WorkMap);
+template __global__ void k_gemm<true, false, float>(const GemmJob*, WorkMap);
+template __global__ void k_gemm<false, true, float>(const GemmJob*, WorkMap);
+template __global__ void k_rayleigh_ritz<double>(Inst*, const int*);
+template __global__ void k_rayleigh_ritz<float>(Inst*, const int*);
+
+}  // namespace sdpg

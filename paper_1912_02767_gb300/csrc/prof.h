@@ -1,0 +1,77 @@
+// prof.h -- launch counting and CUDA-event timing per kernel family.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+namespace sdpg {
+
+struct ProfPending {
+  int fam;
+  cudaEvent_t a, b;
+  double flops, bytes;
+};
+
+struct Prof {
+  bool on = false;
+  long long launches[10] = {};
+  long long timed[10] = {};
+  double ms[10] = {};
+  double flops[10] = {};
+  double bytes[10] = {};
+  std::vector<ProfPending> pending;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t get() {
+    cudaEvent_t e;
+    if (!pool.empty()) {
+      e = pool.back();
+      pool.pop_back();
+    } else {
+      cudaEventCreate(&e);
+    }
+    return e;
+  }
+  void flush() {
+    for (auto& p : pending) {
+      float t = 0.f;
+      if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) {
+        ms[p.fam] += t;
+        timed[p.fam]++;
+      }
+      pool.push_back(p.a);
+      pool.push_back(p.b);
+    }
+    pending.clear();
+  }
+};
+
+Prof& prof();
+
+// Bracket one launch of family `fam` on stream `s`.
+struct ProfScope {
+  int fam;
+  cudaStream_t s;
+  double fl, by;
+  cudaEvent_t a = nullptr;
+  ProfScope(int f, cudaStream_t st, double flops = 0, double bytes = 0) : fam(f), s(st), fl(flops), by(bytes) {
+    Prof& P = prof();
+    P.launches[fam]++;
+    P.flops[fam] += fl;
+    P.bytes[fam] += by;
+    if (P.on) {
+      a = P.get();
+      cudaEventRecord(a, s);
+    }
+  }
+  ~ProfScope() {
+    Prof& P = prof();
+    if (a) {
+      cudaEvent_t b = P.get();
+      cudaEventRecord(b, s);
+      P.pending.push_back({fam, a, b, fl, by});
+      if (P.pending.size() > 8192) P.flush();
+    }
+  }
+};
+
+}  // namespace sdpg

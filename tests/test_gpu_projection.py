@@ -1,0 +1,91 @@
+"""GPU parity of the PSD projection (Eq. 2) computed by LOBPCG (Algorithm 3)
+through the C ABI, against the closed form Pi(Q Lambda Q^T) = Q Lambda_+ Q^T
+and against the oracle's Jacobi projection.  FP64 mode: ||dPi||_F/||W||_F
+<= 1e-6."""
+import numpy as np
+import pytest
+
+from paper_1912_02767_gb300 import instances as gen
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP64 = 1e-6
+
+
+@pytest.fixture(scope="module")
+def sdp():
+    from paper_1912_02767_gb300 import build_lib, sdpgpu
+    build_lib.build()
+    sdpgpu.load()
+    return sdpgpu
+
+
+def closed_form(sp):
+    return (sp["Q"] * np.maximum(sp["lam"], 0)) @ sp["Q"].T
+
+
+@pytest.mark.parametrize("n,f", [(40, 0.1), (64, 0.05), (100, 0.2), (257, 0.03), (300, 0.3)])
+def test_projection_matches_closed_form_and_oracle(sdp, orc, n, f):
+    sp = gen.random_spectrum(n, f, np.random.default_rng(n))
+    ctx = sdp.Context()
+    P, V, info = ctx.project_psd(sp["W"], sp["X0"])
+    ref = closed_form(sp)
+    nW = np.linalg.norm(sp["W"])
+    assert np.linalg.norm(P - ref) / nW <= TOL_FP64
+    Pj, _, _ = orc.psd_project(sp["W"])
+    assert np.linalg.norm(P - Pj) / nW <= TOL_FP64
+    assert info["npos"] == sp["k"]
+    # Theorem 3: ||Pi~ - Pi||_F <= sqrt(2) ||R_+||_F (+ perp term, zero here)
+    assert np.linalg.norm(P - ref) <= np.sqrt(2) * info["res_fro"] + 1e-10 * nW
+
+
+def test_projection_expands_block(sdp):
+    """Start with 3 random columns for 12 positive eigenvalues: the block must
+    grow by random columns (Algorithm 3, expansion) and still be exact."""
+    n, k = 120, 12
+    sp = gen.random_spectrum(n, k / n, np.random.default_rng(5))
+    X0 = np.random.default_rng(6).standard_normal((n, 3))
+    ctx = sdp.Context(lobpcg_max_iter=200)
+    P, V, info = ctx.project_psd(sp["W"], X0, tol=1e-9)
+    assert info["expansions"] >= 1 and info["m"] >= k
+    assert np.linalg.norm(P - closed_form(sp)) / np.linalg.norm(sp["W"]) <= TOL_FP64
+
+
+def test_projection_host_and_device_paths_agree(sdp):
+    torch = pytest.importorskip("torch")
+    n = 130
+    sp = gen.random_spectrum(n, 0.05, np.random.default_rng(9))
+    ctx = sdp.Context()
+    P_h, V_h, _ = ctx.project_psd(sp["W"], sp["X0"], tol=1e-10)
+    Wd = torch.from_numpy(np.ascontiguousarray(sp["W"])).cuda()
+    Xd = torch.from_numpy(np.ascontiguousarray(sp["X0"])).cuda()
+    P_d, V_d, _ = ctx.project_psd(Wd, Xd, tol=1e-10, on_device=True)
+    assert np.abs(P_d.cpu().numpy() - P_h).max() <= 1e-12 * np.abs(P_h).max()
+
+
+def test_projection_degenerate_cases(sdp):
+    ctx = sdp.Context()
+    # negative definite: projection is zero
+    n = 50
+    rng = np.random.default_rng(1)
+    Q = gen.haar_orthogonal(n, rng)
+    W = (Q * -rng.uniform(0.1, 1, n)) @ Q.T
+    P, V, info = ctx.project_psd(W, rng.standard_normal((n, 2)), tol=1e-10)
+    assert np.abs(P).max() <= 1e-9 and info["npos"] == 0
+    # n = 1 and repeated positive eigenvalues
+    P1, _, _ = ctx.project_psd(np.array([[2.5]]), np.array([[1.0]]), tol=1e-12)
+    assert abs(P1[0, 0] - 2.5) < 1e-12
+    lam = np.array([1.0] * 4 + [-1.0] * (n - 4))
+    W = (Q * lam) @ Q.T
+    P, V, info = ctx.project_psd(W, Q[:, :4] + 1e-3 * rng.standard_normal((n, 4)), tol=1e-10)
+    assert np.linalg.norm(P - (Q[:, :4] @ Q[:, :4].T)) <= 1e-8
+
+
+@pytest.mark.parametrize("n,f", [(256, 0.01), (256, 0.05), (256, 0.25), (1024, 0.01), (1024, 0.05)])
+def test_projection_sweep_sizes(sdp, n, f):
+    """Projection-sweep matrices (Haar Q, spectrum U[0.1,1] / U[-1,-0.1],
+    warm start perturbed by 1e-3) at full size against the closed form."""
+    sp = gen.workload_projection(n, f)
+    ctx = sdp.Context()
+    P, V, info = ctx.project_psd(sp["W"], sp["X0"])
+    assert np.linalg.norm(P - closed_form(sp)) / np.linalg.norm(sp["W"]) <= TOL_FP64
