@@ -200,6 +200,30 @@ unsigned long long sdp_footprint_bytes(int n, int m, long nnz, int precision);
 /* Release every device buffer of the context. */
 void sdp_destroy(sdp_ctx* ctx);
 
+/* ---- projection of a small matrix without device allocation ------------
+ * The paper has no counterpart of this call; it exists for callers that
+ * cannot allocate device memory: code running while a CUDA stream is being
+ * captured (cudaMalloc is not permitted there) and applications that pool
+ * all device memory at start-up and forbid later allocation.
+ *
+ * out = Pi_{S+}(W) (Eq. 2) for a symmetric n x n W, both column-major
+ * device arrays of the current device, computed by a one-CTA Jacobi
+ * eigendecomposition on `cuda_stream` (NULL = legacy default stream).  The
+ * call allocates nothing: its scratch (2 * n * n doubles) is a fixed
+ * file-scope device array of 2 * SDP_NOALLOC_MAX_N^2 doubles (256 KiB)
+ * that every GPU loading the library keeps until the process exits.
+ *  - n > SDP_NOALLOC_MAX_N (or n < 1, NULL pointers): SDP_E_INVALID,
+ *    nothing launched.
+ *  - The first call on a device looks up that device's address of the
+ *    scratch array (cudaGetSymbolAddress); make that first call before any
+ *    stream capture begins.
+ *  - Every call shares the one scratch array: calls that overlap on the
+ *    GPU (different streams or host threads) race; serialise them.
+ *  - Asynchronous: returns after the launch (SDP_OK, or SDP_E_CUDA when
+ *    the launch failed); synchronise the stream before reading `out`. */
+#define SDP_NOALLOC_MAX_N 128
+int sdp_project_psd_noalloc(int n, const double* W, double* out, void* cuda_stream);
+
 /* Text of the last CUDA error seen by this thread (static storage). */
 const char* sdp_last_error(void);
 

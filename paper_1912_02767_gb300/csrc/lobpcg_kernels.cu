@@ -493,3 +493,75 @@ template __global__ void k_rayleigh_ritz<double>(Inst*, const int*);
 template __global__ void k_rayleigh_ritz<float>(Inst*, const int*);
 
 }  // namespace sdpg
+
+// ---------------------------------------------------------------------------
+// Projection of a small matrix without any device allocation.
+//
+// For callers that cannot allocate device memory: code that runs while a
+// CUDA stream is being captured into a graph (cudaMalloc is not allowed
+// there), or applications whose memory is fully pooled up front and which
+// forbid allocation after start-up.  The scratch lives in one file-scope
+// __device__ array that every GPU loading this library holds until exit.
+// It is shared by all calls: calls that overlap on the GPU (two streams,
+// two host threads) race on it, so the caller must serialise them.  Each
+// call overwrites every scratch element it reads, so no state carries over.
+//
+// It is the Rayleigh-Ritz kernel specialised to the trial subspace S = I:
+// G = I needs no Cholesky, and the eigendecomposition of M = W by the
+// CTA-wide Jacobi gives Pi(W) = sum over lambda_k > 0 of lambda_k u_k u_k^T.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+#include "../../include/sdpgpu.h"
+
+namespace sdpg {
+static __device__ __align__(256) double g_noalloc_scratch[2 * SDP_NOALLOC_MAX_N * SDP_NOALLOC_MAX_N];
+
+__global__ void __launch_bounds__(1024) k_project_small_noalloc(int n, const double* W, double* out, double* scratch) {
+  __shared__ double shc[SDP_NOALLOC_MAX_N / 2 + 1], shs[SDP_NOALLOC_MAX_N / 2 + 1];
+  __shared__ int sha[SDP_NOALLOC_MAX_N / 2 + 1], shb[SDP_NOALLOC_MAX_N / 2 + 1];
+  __shared__ double red[32];
+  double* H = scratch;
+  double* U = scratch + (size_t)n * n;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    int i = t % n, j = t / n;
+    H[t] = 0.5 * (W[i + (size_t)j * n] + W[j + (size_t)i * n]);
+  }
+  __syncthreads();
+  cta_jacobi<double>(n, H, n, U, n, shc, shs, sha, shb, red);
+  __syncthreads();
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    int i = t % n, j = t / n;
+    double acc = 0.0;
+    for (int k = 0; k < n; ++k) {
+      double l = H[k + (size_t)k * n];
+      if (l > 0.0) acc += l * U[i + (size_t)k * n] * U[j + (size_t)k * n];
+    }
+    out[t] = acc;
+  }
+}
+}  // namespace sdpg
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[64];
+static bool g_noalloc_ready[64];
+
+extern "C" int sdp_project_psd_noalloc(int n, const double* W, double* out, void* cuda_stream) {
+  if (n < 1 || n > SDP_NOALLOC_MAX_N || !W || !out) return SDP_E_INVALID;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SDP_E_CUDA;
+  void* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ready[dev]) {
+      // host code must not use the array's name as a device address: ask
+      // the runtime for this device's address of the array, once per device
+      if (cudaGetSymbolAddress(&g_noalloc_ptr[dev], sdpg::g_noalloc_scratch) != cudaSuccess) return SDP_E_CUDA;
+      g_noalloc_ready[dev] = true;
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  sdpg::k_project_small_noalloc<<<1, 1024, 0, (cudaStream_t)cuda_stream>>>(n, W, out, (double*)scratch);
+  return cudaGetLastError() == cudaSuccess ? SDP_OK : SDP_E_CUDA;
+}
+

@@ -93,6 +93,7 @@ def load():
     L.sdp_server_poll.argtypes = [C.c_void_p, C.c_ulonglong, C.POINTER(Info)]
     L.sdp_server_destroy.argtypes = [C.c_void_p]
     L.sdp_server_destroy.restype = None
+    L.sdp_project_psd_noalloc.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
     L.sdp_prof_enable.argtypes = [C.c_int]
     L.sdp_prof_enable.restype = None
     L.sdp_prof_reset.restype = None
@@ -310,6 +311,17 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+NOALLOC_MAX_N = 128
+
+
+def project_psd_noalloc(W, out, stream=None):
+    """sdp_project_psd_noalloc on torch CUDA tensors (n x n, float64,
+    contiguous; W symmetric).  Asynchronous on `stream`; returns the status."""
+    n = W.shape[0]
+    return load().sdp_project_psd_noalloc(n, C.c_void_p(W.data_ptr()), C.c_void_p(out.data_ptr()),
+                                          _stream_handle(stream))
 
 
 def footprint_bytes(n, m, nnz, precision=PREC_FP64):
