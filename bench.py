@@ -199,17 +199,26 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     nbytes_W = sum(m["n"] * m["n"] * 8 for m in mats)
 
-    def step():
+    tol_scale = 0.5e-6 if args.prec == "fp64" else 1e-5
+    tols = [tol_scale * float(np.linalg.norm(m["W"])) / np.sqrt(2.0 * m["k"]) for m in mats]
+    per_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in mats]
+
+    def step(timed=False):
         infos = []
-        for m, Wd, X0, V, out in dev:
+        for q, (m, Wd, X0, V, out) in enumerate(dev):
             V.copy_(X0)
-            info = ctx.project_raw(m["n"], Wd.data_ptr(), out.data_ptr(), V.data_ptr(), m["k"], m["n"], 0.0, True)
+            if timed:
+                per_ev[q][0].record(stream)
+            info = ctx.project_raw(m["n"], Wd.data_ptr(), out.data_ptr(), V.data_ptr(), m["k"], m["n"], tols[q], True)
+            if timed:
+                per_ev[q][1].record(stream)
             infos.append(info)
         return infos
 
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
+    sdpgpu.prof_reset()
     # correctness of the measured path on every matrix (closed form)
     errs = []
     for (m, Wd, X0, V, out) in dev:
@@ -225,13 +234,17 @@ def main():
     torch.cuda.synchronize()
     clocks.start()
     step_ms = []
+    per_ms = [0.0] * len(mats)
+    last_infos = None
     for s in range(args.steps):
         flush.zero_()
         ev[s][0].record(stream)
-        step()
+        last_infos = step(timed=True)
         ev[s][1].record(stream)
         torch.cuda.synchronize()
         step_ms.append(ev[s][0].elapsed_time(ev[s][1]))
+        for q in range(len(mats)):
+            per_ms[q] += per_ev[q][0].elapsed_time(per_ev[q][1]) / args.steps
     torch.cuda.synchronize()
     ck = clocks.stop()
     sdpgpu.prof_enable(False)
@@ -292,7 +305,10 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single"},
                 "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": ck, "max_rel_err_vs_closed_form": max(errs),
-                "per_matrix_err": errs}
+                "per_matrix": [{"n": m["n"], "k": m["k"], "ms": round(per_ms[q], 3), "rel_err": errs[q],
+                                "rr_steps": last_infos[q]["steps"], "m": last_infos[q]["m"],
+                                "jacobi_sweeps": last_infos[q]["jacobi_sweeps"],
+                                "converged": last_infos[q]["converged"]} for q, m in enumerate(mats)]}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

@@ -105,6 +105,7 @@ typedef struct {
   int converged;       /* 1 if every Ritz residual met tol                 */
   double res_fro;      /* ||R_+||_F over the positive Ritz pairs: Thm 3 gives */
                        /* ||Pi~ - Pi||_F <= sqrt(2)*res_fro (+ the perp term) */
+  int jacobi_sweeps;   /* Jacobi sweeps summed over the Rayleigh-Ritz steps  */
 } sdp_proj_info;
 
 /* Fill *s with the defaults listed above. */
@@ -166,6 +167,15 @@ int sdp_get_certificate(sdp_ctx* ctx, double* cert_y, double* cert_M, int to_dev
  * sdp_setup.  Errors: SDP_E_INVALID, SDP_E_NUMERICAL, SDP_E_NOMEM. */
 int sdp_project_psd(sdp_ctx* ctx, int n, const double* W, double* out, double* V_warm, int* m_inout,
                     int mcap, double tol, int on_device, sdp_proj_info* info);
+
+/* The LOBPCG block product (Algorithm 3: A X, A R): out = W B for a
+ * symmetric n x n W and an n x k block B, all column-major device arrays,
+ * in the context's precision: SDP_PREC_FP64 on the CUDA cores, otherwise
+ * split-BF16 x3 on the tcgen05 tensor cores with FP32 accumulation.
+ * resplit_w = 0 reuses the bf16 split of the W passed last time (same n),
+ * so repeated products with one W convert it once.  k <= ceil(n/3) + 2b.
+ * Errors: SDP_E_INVALID, SDP_E_NOMEM, SDP_E_CUDA. */
+int sdp_block_product(sdp_ctx* ctx, int n, const double* W, const double* B, int k, double* out, int resplit_w);
 
 /* Solve `count` set-up contexts together: every ADMM step of all of them is
  * issued as one batched launch sequence (one launch per kernel for the

@@ -186,6 +186,9 @@ static size_t layout_bytes(const Layout& L, Inst* inst, char* base) {
   size_t o_E = a.take<double>(nn), o_EV = a.take<double>(nn), o_el = a.take<double>(2 * (size_t)L.n),
          o_er2 = a.take<double>(2 * (size_t)L.n + 2), o_eo = a.take<int>(L.n);
   size_t o_ctl = a.take<Ctl>(1), o_chk = a.take<Check>(1);
+  size_t o_whi = a.take<uint16_t>(nn), o_wlo = a.take<uint16_t>(nn);
+  size_t o_bhi = a.take<uint16_t>((size_t)L.ld * L.mcap), o_blo = a.take<uint16_t>((size_t)L.ld * L.mcap);
+  size_t o_tcp = a.take<float>((size_t)8 * L.ld * L.mcap);
   if (inst && base) {
     memset(inst, 0, sizeof(*inst));
     inst->n = L.n; inst->ld = L.ld; inst->mc = L.mc; inst->nent = L.nent; inst->mcap = L.mcap;
@@ -213,6 +216,8 @@ static size_t layout_bytes(const Layout& L, Inst* inst, char* base) {
     inst->E = (double*)(base + o_E); inst->EV = (double*)(base + o_EV); inst->elam = (double*)(base + o_el);
     inst->erot = (double*)(base + o_er2); inst->eord = (int*)(base + o_eo);
     inst->ctl = (Ctl*)(base + o_ctl); inst->chk = (Check*)(base + o_chk);
+    inst->Whi = base + o_whi; inst->Wlo = base + o_wlo; inst->Bhi = base + o_bhi; inst->Blo = base + o_blo;
+    inst->tcpart = (float*)(base + o_tcp);
   }
   return a.off;
 }

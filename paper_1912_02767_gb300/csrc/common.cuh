@@ -13,6 +13,19 @@ namespace sdpg {
 
 enum { MODE_POS = 0, MODE_NEG = 1, MODE_EXACT = 2 };
 
+// Jacobi rotation rule: rotate the pair (a, b) only while
+//   |h_ab| > max(rel * sqrt(|h_aa h_bb|), abs_thr),  abs_thr = eps ||H||_F / n
+// with rel = 0: the off-diagonal Frobenius norm left is below eps ||H||_F.
+// A relative rule (rel > 0) leaves eigenvectors inside clusters of close
+// Ritz values too inaccurate for the per-pair residual test of LOBPCG, so
+// it is not used.  A sweep without rotations ends the iteration.
+constexpr double kJacobiRel64 = 0.0, kJacobiAbs64 = 4e-16;
+constexpr double kJacobiRel32 = 0.0, kJacobiAbs32 = 4e-7;
+__device__ __forceinline__ bool jacobi_rotates(double hab, double haa, double hbb, double rel, double abs_thr) {
+  double t = rel * sqrt(fabs(haa * hbb));
+  return fabs(hab) > (t > abs_thr ? t : abs_thr);
+}
+
 // Per-instance control block (device memory, read back by the host).
 struct Ctl {
   int mode;      // projection mode of the current ADMM iteration
@@ -96,11 +109,23 @@ struct Inst {
   // mixed precision operands (bf16 hi/lo of W and of the multiplied block)
   void *Whi, *Wlo, *Bhi, *Blo;
   float* Wf;            // FP32 copy of W (mixed mode reconstruction operand)
+  float* tcpart;        // split-K partials of the tensor-core product (8 x ld x mcap)
   Ctl* ctl;
   Check* chk;
   double* chk_part;     // per-CTA partials of the check
   int prec;             // sdp_precision
   int pad1;
+};
+
+// State of a grid-wide barrier and of the cooperative kernels using it.
+struct GridBar {
+  unsigned count, gen;
+  int err;     // a barrier wait gave up (bounded spin)
+  int fail;    // Cholesky breakdown column (1-based), 0 if none
+  int sweeps;  // Jacobi sweeps done
+  int pad;
+  double fro2; // ||H||_F^2
+  int rot[64]; // rotations per sweep
 };
 
 // Prefix map from a flat block index to (instance, local unit).

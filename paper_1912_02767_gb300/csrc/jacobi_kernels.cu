@@ -19,6 +19,40 @@ __device__ __forceinline__ void jac_pair(int r, int k, int np, int* a, int* b) {
   }
 }
 
+// ||A||_F^2 of a rows x cols matrix in a fixed summation order (one CTA):
+// the Jacobi threshold derived from it must not depend on scheduling, so
+// that an instance gets bit-identical rotations alone and in a batch.
+__device__ double cta_fro2_det(const double* A, int ld, int rows, int cols) {
+  __shared__ double sh[1024];
+  double part = 0.0;
+  const long tot = (long)rows * cols;
+  for (long t = threadIdx.x; t < tot; t += blockDim.x) {
+    double a = A[idx2((int)(t % rows), (int)(t / rows), ld)];
+    part += a * a;
+  }
+  sh[threadIdx.x] = part;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// ||W||_F^2 of each listed instance into ctl->jac_off (deterministic)
+__global__ void k_fro2_det(Inst* insts, const int* list) {
+  const Inst& I = insts[list[blockIdx.x]];
+  double v = cta_fro2_det(I.W, I.ld, I.n, I.n);
+  if (threadIdx.x == 0) I.ctl->jac_off = v;
+}
+
+__global__ void k_fro2_mat(const double* A, int ld, int rows, int cols, double* dst) {
+  double v = cta_fro2_det(A, ld, rows, cols);
+  if (threadIdx.x == 0) *dst = v;
+}
+
 // ||W||_F^2 into ctl->jac_off (ctl->jac_off zeroed by the host)
 __global__ void k_fro2(Inst* insts, WorkMap wm) {
   __shared__ double sh[32];
@@ -71,10 +105,10 @@ __global__ void k_jac_angles(Inst* insts, WorkMap wm, int round) {
   jac_pair(round, k, np, &a, &b);
   double c = 1.0, s = 0.0;
   if (a < n && b < n) {
-    double thr = 1e-15 * sqrt(I.ctl->jac_off) / (double)n;
+    double thr = kJacobiAbs64 * sqrt(I.ctl->jac_off) / (double)n;
     double hab = I.E[idx2(a, b, I.ld)];
-    if (fabs(hab) > thr) {
-      double haa = I.E[idx2(a, a, I.ld)], hbb = I.E[idx2(b, b, I.ld)];
+    double haa = I.E[idx2(a, a, I.ld)], hbb = I.E[idx2(b, b, I.ld)];
+    if (jacobi_rotates(hab, haa, hbb, kJacobiRel64, thr)) {
       double tau = (hbb - haa) / (2.0 * hab);
       double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
       c = 1.0 / sqrt(1.0 + t * t);

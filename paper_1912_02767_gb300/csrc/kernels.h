@@ -39,11 +39,27 @@ __global__ void k_gemm(const GemmJob* jobs, WorkMap wm);
 __global__ void k_gram_reduce(const GemmJob* jobs, WorkMap wm, int symmetrize);
 template <typename T>
 __global__ void k_rayleigh_ritz(Inst* insts, const int* list);
+template <typename T>
+__global__ void k_rr_smem(Inst* insts, const int* list);
+// largest trial subspace k_rr_smem<T> holds (2 p^2 elements of T <= 200 KiB)
+constexpr int kRRSmemMaxF32 = 160;
+constexpr int kRRSmemMaxF64 = 112;
 __global__ void k_resid(Inst* insts, WorkMap wm);
 __global__ void k_resid_finish(Inst* insts, const int* list, int last_allowed);
 __global__ void k_compact(Inst* insts, WorkMap wm);
 __global__ void k_fill_random(Inst* insts, WorkMap wm, const int* col0, const int* ncols, const int* draw,
                               const unsigned* stream, unsigned long long seed);
+
+// rr_large.cu (cooperative, one matrix per launch)
+template <typename T>
+__global__ void k_chol_inv_coop(double* G, double* Linv, int p, double piv_min, GridBar* b);
+template <typename T>
+__global__ void k_jacobi_coop(double* H, double* H2, int ldh, double* U, int ldu, int p, double rel, double abs_eps,
+                              int max_sweeps, const double* fro2, GridBar* b);
+__global__ void k_diag_rank(const double* H, int ldh, int p, int* ord);
+__global__ void k_select_top(const double* H, int ldh, const double* U, int ldu, int p, int keep, const int* ord,
+                             double* Usel, double* theta, int* npos);
+__global__ void k_rr_large_finish(Ctl* ctl, const GridBar* b);
 
 // jacobi_kernels.cu (exact branch)
 __global__ void k_jac_init(Inst* insts, WorkMap wm, int negate);
@@ -52,7 +68,14 @@ __global__ void k_jac_apply(Inst* insts, WorkMap wm, int round);
 __global__ void k_jac_sort(Inst* insts, const int* list);
 __global__ void k_jac_gather(Inst* insts, WorkMap wm);
 __global__ void k_fro2(Inst* insts, WorkMap wm);
+__global__ void k_fro2_det(Inst* insts, const int* list);
+__global__ void k_fro2_mat(const double* A, int ld, int rows, int cols, double* dst);
 __global__ void k_seed_block(Inst* insts, WorkMap wm);
 __global__ void k_copy_cols(const double* src, int lds, double* dst, int ldd, int rows, int cols, double scale);
+
+// tc_gemm.cu (host wrappers)
+int tc_wprod(cudaStream_t s, const void* whi, const void* wlo, int ldw, const void* bhi, const void* blo, int ldb,
+             int n, int N, double alpha, double* out, int ldo, float* part, int* err, int num_sms);
+void split_bf16(cudaStream_t s, const double* src, int lds, int rows, int cols, void* hi, void* lo, int ldd);
 
 }  // namespace sdpg

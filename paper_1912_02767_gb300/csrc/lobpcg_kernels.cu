@@ -132,13 +132,13 @@ template <typename T>
 struct RRConst;
 template <>
 struct RRConst<double> {
-  static constexpr double jac_eps = 4e-16;
+  static constexpr double jac_rel = kJacobiRel64, jac_abs = kJacobiAbs64;
   static constexpr double piv_min = 1e-12;
   static constexpr int max_sweeps = 40;
 };
 template <>
 struct RRConst<float> {
-  static constexpr double jac_eps = 4e-7;
+  static constexpr double jac_rel = kJacobiRel32, jac_abs = kJacobiAbs32;
   static constexpr double piv_min = 1e-6;
   static constexpr int max_sweeps = 25;
 };
@@ -176,7 +176,7 @@ __device__ int cta_jacobi(int p, double* H, int ldh, double* U, int ldu, double*
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-    thr = RRConst<T>::jac_eps * sqrt(s) / (double)(p > 0 ? p : 1);
+    thr = RRConst<T>::jac_abs * sqrt(s) / (double)(p > 0 ? p : 1);
   }
   __syncthreads();
   int sweep = 0;
@@ -191,8 +191,8 @@ __device__ int cta_jacobi(int p, double* H, int ldh, double* U, int ldu, double*
         double c = 1.0, s = 0.0;
         if (a < p && b < p) {
           T hab = (T)H[idx2(a, b, ldh)];
-          if (fabs((double)hab) > thr) {
-            T haa = (T)H[idx2(a, a, ldh)], hbb = (T)H[idx2(b, b, ldh)];
+          T haa = (T)H[idx2(a, a, ldh)], hbb = (T)H[idx2(b, b, ldh)];
+          if (jacobi_rotates((double)hab, (double)haa, (double)hbb, RRConst<T>::jac_rel, thr)) {
             T tau = (hbb - haa) / ((T)2 * hab);
             T tt = (tau >= (T)0 ? (T)1 : (T)-1) / (fabs(tau) + sqrt((T)1 + tau * tau));
             T cc = (T)1 / sqrt((T)1 + tt * tt);
@@ -565,3 +565,190 @@ extern "C" int sdp_project_psd_noalloc(int n, const double* W, double* out, void
   return cudaGetLastError() == cudaSuccess ? SDP_OK : SDP_E_CUDA;
 }
 
+
+namespace sdpg {
+// ---------------------------------------------------------------------------
+// Rayleigh-Ritz for small trial subspaces with every matrix in shared
+// memory (one CTA per instance): the same steps as k_rayleigh_ritz --
+// Cholesky of G, L^{-1}, H = L^{-1} M L^{-T}, parallel cyclic Jacobi, sort,
+// Coef = L^{-T} U_top -- without global-memory round trips inside the
+// Jacobi rounds.  Capacity: 2 p^2 elements of T in shared memory.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(1024) k_rr_smem(Inst* insts, const int* list) {
+  const Inst& I = insts[list[blockIdx.x]];
+  Ctl* ctl = I.ctl;
+  const int p = ctl->p, keep = ctl->keep;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* A = (T*)smraw;      // p x p
+  T* B = A + p * p;      // p x p
+  __shared__ T cs[2][160];
+  __shared__ short pa[160], pb[160];
+  __shared__ int ord[320];
+  __shared__ int fail, rotated;
+  __shared__ double red[32];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int np = p + (p & 1), P2 = np / 2;
+  // 1. A = G, Cholesky in place (lower)
+  for (int t = tid; t < p * p; t += nt) A[t] = (T)I.G[t];
+  if (tid == 0) fail = 0;
+  __syncthreads();
+  for (int j = 0; j < p; ++j) {
+    if (tid == 0) {
+      T d = A[j + j * p];
+      if (!(d > (T)RRConst<T>::piv_min)) fail = j + 1;
+      A[j + j * p] = sqrt(d > (T)0 ? d : (T)1);
+    }
+    __syncthreads();
+    if (fail) break;
+    T ljj = A[j + j * p];
+    for (int i = j + 1 + tid; i < p; i += nt) A[i + j * p] /= ljj;
+    __syncthreads();
+    int w = p - j - 1;
+    for (int t = tid; t < w * w; t += nt) {
+      int r = t % w, c = t / w;
+      if (r < c) continue;
+      A[(j + 1 + r) + (j + 1 + c) * p] -= A[(j + 1 + r) + j * p] * A[(j + 1 + c) + j * p];
+    }
+    __syncthreads();
+  }
+  if (fail) {
+    if (tid == 0) ctl->rr_fail = fail;
+    return;
+  }
+  // 2. B = L^{-1}: column c by one thread (p <= 160 threads busy)
+  for (int c = tid; c < p; c += nt) {
+    for (int i = 0; i < c; ++i) B[i + c * p] = (T)0;
+    for (int i = c; i < p; ++i) {
+      T acc = (i == c) ? (T)1 : (T)0;
+      for (int k = c; k < i; ++k) acc -= A[i + k * p] * B[k + c * p];
+      B[i + c * p] = acc / A[i + i * p];
+    }
+  }
+  __syncthreads();
+  // keep L^{-1} in global for the coefficients; T1 = Linv M -> global scratch
+  for (int t = tid; t < p * p; t += nt) I.Linv[t] = (double)B[t];
+  for (int t = tid; t < p * p; t += nt) {
+    int i = t % p, j = t / p;
+    T acc = 0;
+    for (int k = 0; k <= i; ++k) acc += B[i + k * p] * (T)I.M[k + j * p];
+    I.H[t] = (double)acc;
+  }
+  __syncthreads();
+  // 3. A = H = T1 Linv^T (symmetric: lower computed, mirrored)
+  for (int t = tid; t < p * p; t += nt) {
+    int i = t % p, j = t / p;
+    if (i < j) continue;
+    T acc = 0;
+    for (int k = 0; k <= j; ++k) acc += (T)I.H[i + k * p] * B[j + k * p];
+    A[i + j * p] = acc;
+    A[j + i * p] = acc;
+  }
+  __syncthreads();
+  // 4. Jacobi on A, rotations accumulated in B (= U)
+  for (int t = tid; t < p * p; t += nt) B[t] = (t % p == t / p) ? (T)1 : (T)0;
+  double part = 0.0;
+  for (int t = tid; t < p * p; t += nt) part += (double)A[t] * (double)A[t];
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+  if ((tid & 31) == 0) red[tid >> 5] = part;
+  __syncthreads();
+  __shared__ double thr;
+  if (tid == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (nt >> 5); ++w) s += red[w];
+    thr = RRConst<T>::jac_abs * sqrt(s) / (double)p;
+  }
+  __syncthreads();
+  int sweeps = 0;
+  for (int sweep = 0; sweep < RRConst<T>::max_sweeps && p >= 2; ++sweep) {
+    if (tid == 0) rotated = 0;
+    __syncthreads();
+    for (int r = 0; r < np - 1; ++r) {
+      for (int k = tid; k < P2; k += nt) {
+        int a, b;
+        rr_pair(r, k, np, &a, &b);
+        T c = (T)1, s = (T)0;
+        if (a < p && b < p) {
+          T hab = A[a + b * p];
+          T haa = A[a + a * p], hbb = A[b + b * p];
+          if (jacobi_rotates((double)hab, (double)haa, (double)hbb, RRConst<T>::jac_rel, thr)) {
+            T tau = (hbb - haa) / ((T)2 * hab);
+            T tt = (tau >= (T)0 ? (T)1 : (T)-1) / (fabs(tau) + sqrt((T)1 + tau * tau));
+            c = (T)1 / sqrt((T)1 + tt * tt);
+            s = tt * c;
+            rotated = 1;
+          }
+        }
+        cs[0][k] = c; cs[1][k] = s; pa[k] = (short)a; pb[k] = (short)b;
+      }
+      __syncthreads();
+      for (int e = tid; e < P2 * P2; e += nt) {
+        int ki = e % P2, kj = e / P2;
+        T si = cs[1][ki], sj = cs[1][kj];
+        if (si == (T)0 && sj == (T)0) continue;
+        int ai = pa[ki], bi = pb[ki], aj = pa[kj], bj = pb[kj];
+        T ci = cs[0][ki], cj = cs[0][kj];
+        bool vai = ai < p, vbi = bi < p, vaj = aj < p, vbj = bj < p;
+        T haa = (vai && vaj) ? A[ai + aj * p] : (T)0;
+        T hab = (vai && vbj) ? A[ai + bj * p] : (T)0;
+        T hba = (vbi && vaj) ? A[bi + aj * p] : (T)0;
+        T hbb = (vbi && vbj) ? A[bi + bj * p] : (T)0;
+        T taa = cj * haa - sj * hab, tab = sj * haa + cj * hab;
+        T tba = cj * hba - sj * hbb, tbb = sj * hba + cj * hbb;
+        T naa = ci * taa - si * tba, nba = si * taa + ci * tba;
+        T nab = ci * tab - si * tbb, nbb = si * tab + ci * tbb;
+        if (ki == kj && si != (T)0) { nab = (T)0; nba = (T)0; }
+        if (vai && vaj) A[ai + aj * p] = naa;
+        if (vai && vbj) A[ai + bj * p] = nab;
+        if (vbi && vaj) A[bi + aj * p] = nba;
+        if (vbi && vbj) A[bi + bj * p] = nbb;
+      }
+      for (int e = tid; e < p * P2; e += nt) {
+        int row = e % p, k = e / p;
+        T s = cs[1][k];
+        if (s == (T)0) continue;
+        int a = pa[k], b = pb[k];
+        if (a >= p || b >= p) continue;
+        T c = cs[0][k];
+        T ua = B[row + a * p], ub = B[row + b * p];
+        B[row + a * p] = c * ua - s * ub;
+        B[row + b * p] = s * ua + c * ub;
+      }
+      __syncthreads();
+    }
+    ++sweeps;
+    if (!rotated) break;
+    __syncthreads();
+  }
+  // 5. ascending order
+  for (int i = tid; i < p; i += nt) {
+    T li = A[i + i * p];
+    int rank = 0;
+    for (int j = 0; j < p; ++j) {
+      T lj = A[j + j * p];
+      rank += (lj < li) || (lj == li && j < i);
+    }
+    ord[rank] = i;
+  }
+  __syncthreads();
+  // 6. Coef = Linv^T U[:, top keep]
+  for (int t = tid; t < p * keep; t += nt) {
+    int i = t % p, j = t / p;
+    int col = ord[p - keep + j];
+    T acc = 0;
+    for (int k = i; k < p; ++k) acc += (T)I.Linv[k + i * p] * B[k + col * p];
+    I.Coef[i + j * p] = (double)acc;
+  }
+  for (int j = tid; j < keep; j += nt) I.theta[j] = (double)A[ord[p - keep + j] * (p + 1)];
+  if (tid == 0) {
+    int c = 0;
+    for (int j = 0; j < p; ++j) c += A[j + j * p] > (T)0;
+    ctl->npos_rr = c;
+    ctl->rr_fail = 0;
+    ctl->sweeps += sweeps;
+  }
+}
+
+template __global__ void k_rr_smem<double>(Inst*, const int*);
+template __global__ void k_rr_smem<float>(Inst*, const int*);
+}  // namespace sdpg

@@ -42,7 +42,8 @@ class Info(C.Structure):
 
 class ProjInfo(C.Structure):
     _fields_ = [("status", C.c_int), ("steps", C.c_int), ("m", C.c_int), ("npos", C.c_int),
-                ("expansions", C.c_int), ("converged", C.c_int), ("res_fro", C.c_double)]
+                ("expansions", C.c_int), ("converged", C.c_int), ("res_fro", C.c_double),
+                ("jacobi_sweeps", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -93,6 +94,7 @@ def load():
     L.sdp_server_poll.argtypes = [C.c_void_p, C.c_ulonglong, C.POINTER(Info)]
     L.sdp_server_destroy.argtypes = [C.c_void_p]
     L.sdp_server_destroy.restype = None
+    L.sdp_block_product.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int]
     L.sdp_project_psd_noalloc.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
     L.sdp_prof_enable.argtypes = [C.c_int]
     L.sdp_prof_enable.restype = None
@@ -235,6 +237,14 @@ class Context:
                                       C.byref(mm), mcap, tol, 0, C.byref(info))
         _check(rc, "sdp_project_psd")
         return out, np.array(Vbuf[:, : mm.value]), info.as_dict()
+
+    def block_product(self, W, B, out, resplit_w=True):
+        """out = W B (torch CUDA float64 tensors; W symmetric n x n, B and out
+        column-major n x k, i.e. torch shape (k, n))."""
+        n = W.shape[0]
+        k = B.shape[0]
+        _check(self.lib.sdp_block_product(self.h, n, C.c_void_p(W.data_ptr()), C.c_void_p(B.data_ptr()), k,
+                                          C.c_void_p(out.data_ptr()), 1 if resplit_w else 0), "sdp_block_product")
 
     def project_raw(self, n, W_ptr, out_ptr, V_ptr, m, mcap, tol, on_device):
         """sdp_project_psd on raw pointers (column-major n x n W and out,

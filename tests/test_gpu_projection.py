@@ -89,3 +89,39 @@ def test_projection_sweep_sizes(sdp, n, f):
     ctx = sdp.Context()
     P, V, info = ctx.project_psd(sp["W"], sp["X0"])
     assert np.linalg.norm(P - closed_form(sp)) / np.linalg.norm(sp["W"]) <= TOL_FP64
+
+
+@pytest.mark.parametrize("n,f", [(300, 0.2), (1024, 0.05)])
+def test_projection_mixed_precision(sdp, n, f):
+    """Mixed path (FP32 Grams / Rayleigh-Ritz, FP64 residual norms): the error
+    against the closed form is reported and bounded by the FP32 level."""
+    sp = gen.random_spectrum(n, f, np.random.default_rng(77 + n))
+    ctx = sdp.Context(precision=sdp.PREC_BF16X3)
+    nW = np.linalg.norm(sp["W"])
+    P, V, info = ctx.project_psd(sp["W"], sp["X0"], tol=1e-5 * nW / np.sqrt(2 * sp["k"]))
+    err = np.linalg.norm(P - closed_form(sp)) / nW
+    assert err <= 1e-4, err
+    assert info["npos"] == sp["k"]
+
+
+@pytest.mark.parametrize("n,k", [(64, 8), (200, 37), (1024, 51), (1000, 300), (4096, 205)])
+def test_block_product_tensor_cores(sdp, n, k):
+    """W B on the tcgen05 tensor cores (split-BF16 x3, FP32 accumulation)
+    against an FP64 product: relative error at the bf16-split level; FP64
+    mode exact to rounding.  Sizes span several 128-row tiles, ragged
+    tails, N tiles up to 256 and split-K."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(n + k)
+    A = rng.standard_normal((n, n))
+    W = 0.5 * (A + A.T)
+    B = rng.standard_normal((n, k))
+    ref = W @ B
+    Wd = torch.from_numpy(np.ascontiguousarray(W)).cuda()
+    Bd = torch.from_numpy(np.ascontiguousarray(B.T)).cuda()   # column-major n x k
+    for prec, tol in [(sdp.PREC_FP64, 1e-13), (sdp.PREC_BF16X3, 3e-5)]:
+        ctx = sdp.Context(precision=prec)
+        out = torch.full((k, n), float("nan"), dtype=torch.float64, device="cuda")
+        ctx.block_product(Wd, Bd, out)
+        got = out.cpu().numpy().T
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert np.all(np.isfinite(got)) and err <= tol, (prec, err)
