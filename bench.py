@@ -35,12 +35,64 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "bf16x3"])
+    ap.add_argument("--prec", default="bf16x3", choices=["fp64", "bf16x3"])
+    ap.add_argument("--no-fp64-path", action="store_true", help="skip timing the plain FP64 path beside")
     ap.add_argument("--sizes", default="256,1024,4096")
     ap.add_argument("--fracs", default="0.01,0.05,0.25")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "maxcut64", "theta500", "batch", "serve"],
+                    help="sweep: the projection sweep (the bench line); the others time ADMM solves")
+    ap.add_argument("--count", type=int, default=64, help="instances (batch) or requests (serve)")
+    ap.add_argument("--kernel", default=None, choices=[None, "product"],
+                    help="time one kernel alone: 'product' = W B on the tensor cores (sdp_block_product)")
+    ap.add_argument("--n", type=int, default=6144)
+    ap.add_argument("--k", type=int, default=256)
+    ap.add_argument("--iters", type=int, default=20)
     return ap.parse_args()
+
+
+def run_product(args):
+    """The block product W B (Algorithm 3's A X) alone: W split once, then
+    `iters` products; achieved bytes = split W (4 n^2) + split B (4 n k) +
+    FP64 result (8 n k) per launch, flops = 2 n^2 k."""
+    import torch
+    from paper_1912_02767_gb300 import build_lib, sdpgpu
+    build_lib.build()
+    sdpgpu.load()
+    prec = sdpgpu.PREC_FP64 if args.prec == "fp64" else sdpgpu.PREC_BF16X3
+    n, k = args.n, args.k
+    g = torch.Generator(device="cuda").manual_seed(1)
+    A = torch.randn((n, n), dtype=torch.float64, device="cuda", generator=g)
+    W = 0.5 * (A + A.t())
+    del A
+    B = torch.randn((k, n), dtype=torch.float64, device="cuda", generator=g)
+    out = torch.empty_like(B)
+    stream = torch.cuda.current_stream()
+    ctx = sdpgpu.Context(stream=stream, precision=prec)
+    ctx.block_product(W, B, out, resplit_w=True)
+    for _ in range(3):
+        ctx.block_product(W, B, out, resplit_w=False)
+    torch.cuda.synchronize()
+    ref = (W @ B.t()).t()
+    err = float((out - ref).norm() / ref.norm())
+    sdpgpu.prof_reset()
+    sdpgpu.prof_enable(True)
+    for _ in range(args.iters):
+        ctx.block_product(W, B, out, resplit_w=False)
+    torch.cuda.synchronize()
+    sdpgpu.prof_enable(False)
+    pr = sdpgpu.prof_get()["product"]
+    ms = pr["ms"] / max(pr["timed"], 1)
+    gbs = pr["bytes"] / max(pr["timed"], 1) / (ms / 1000.0) / 1e9
+    tfl = pr["flops"] / max(pr["timed"], 1) / (ms / 1000.0) / 1e12
+    pk = peaks()
+    line = {"kernel": "block product W B", "precision": args.prec, "n": n, "k": k, "avg_launch_ms": ms,
+            "achieved_gbs": gbs, "hbm_peak_gbs": pk.get("hbm_gbs"), "frac_hbm": gbs / pk.get("hbm_gbs", 6800.0),
+            "algorithmic_tflops": tfl, "executed_tflops": tfl * (3 if args.prec != "fp64" else 1),
+            "bf16_peak_tflops": pk.get("bf16_tflops"), "rel_err_vs_fp64": err, "launches": pr["timed"],
+            "bytes_per_launch": pr["bytes"] / max(pr["timed"], 1)}
+    print(json.dumps(line), flush=True)
 
 
 def sweep(args):
@@ -167,10 +219,150 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _ctx_for(sdpgpu, inst, stream, prec, **kw):
+    c = sdpgpu.Context(stream=stream, precision=prec, **kw)
+    c.setup(inst)
+    return c
+
+
+def run_admm(args):
+    """ADMM solves (Algorithm 1 + Algorithm 3) on the ADMM workloads:
+    maxcut64: max-cut n = 64, p = 0.1, rho = 1, residual 1e-4: solves/s of the
+              FP64 path, the mixed path and the exact-eigendecomposition
+              comparator, objective checked against the FP64 oracle;
+    theta500: Lovasz theta n = 500, p = 0.2, rho = 10, mixed precision;
+    batch:    `count` max-cut instances, n ~ U{64..1024}, p ~ U[0.02, 0.2],
+              solved together by sdp_batch_solve vs one by one (FP64 path);
+    serve:    `count` Poisson requests (50/s) into the continuous-batching
+              server; p50/p99 latency from arrival to result."""
+    import torch
+    from paper_1912_02767_gb300 import build_lib, sdpgpu
+    build_lib.build()
+    sdpgpu.load()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    P64, PMX = sdpgpu.PREC_FP64, sdpgpu.PREC_BF16X3
+    out = {"workload": args.workload}
+    if args.workload == "maxcut64":
+        inst = gen.workload_maxcut64(0)
+        import importlib
+        importlib.import_module("oracle.build").build()
+        import oracle
+        cons = oracle.Constraints(inst.n, inst.m, inst.cp, inst.ci, inst.cj, inst.cv)
+        t0 = time.perf_counter()
+        ref = oracle.admm_solve(inst.n, inst.C, cons, inst.b, eps_abs=1e-4)
+        t_or = time.perf_counter() - t0
+        for name, kw in [("fp64", dict(precision=P64)), ("mixed", dict(precision=PMX)),
+                         ("exact_eig_fp64", dict(precision=P64, exact_only=1))]:
+            c = sdpgpu.Context(stream=stream, eps_abs=1e-4, **kw).setup(inst)
+            c.solve()
+            reps = max(1, args.steps)
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                r = c.solve()
+            dt = (time.perf_counter() - t0) / reps
+            out[name] = {"solves_per_s": 1.0 / dt, "ms": 1000 * dt, "iters": r["iters"], "status": r["status_name"],
+                         "obj": r["obj"], "rel_obj_err_vs_oracle": abs(r["obj"] - ref["obj"]) / abs(ref["obj"]),
+                         "n_lobpcg": r["n_lobpcg"], "n_exact": r["n_exact"], "lobpcg_steps": r["lobpcg_steps"]}
+        out["oracle_exact_cpu"] = {"solves_per_s": 1.0 / t_or, "iters": ref["iters"], "obj": ref["obj"], "cores": 1}
+    elif args.workload == "theta500":
+        inst = gen.workload_theta500(0)
+        for name, prec in [("mixed", PMX), ("fp64", P64)]:
+            c = sdpgpu.Context(stream=stream, precision=prec, eps_abs=1e-4, rho=10.0).setup(inst)
+            t0 = time.perf_counter()
+            r = c.solve()
+            dt = time.perf_counter() - t0
+            out[name] = {"solves_per_s": 1.0 / dt, "s": dt, "iters": r["iters"], "status": r["status_name"],
+                         "obj": r["obj"], "r_prim": r["r_prim"], "r_dual": r["r_dual"], "rank": r["rank"],
+                         "n_lobpcg": r["n_lobpcg"], "n_exact": r["n_exact"]}
+    elif args.workload == "batch":
+        insts = gen.workload_batch(args.count)
+        ctxs = [_ctx_for(sdpgpu, i, stream, PMX, eps_abs=1e-4) for i in insts]
+        t0 = time.perf_counter()
+        infos = sdpgpu.batch_solve(ctxs)
+        dt = time.perf_counter() - t0
+        out["mixed_batched"] = {"solves_per_s": len(insts) / dt, "s": dt,
+                                "statuses": {k: sum(1 for i in infos if i["status_name"] == k)
+                                             for k in set(i["status_name"] for i in infos)},
+                                "iters_max": max(i["iters"] for i in infos)}
+        print("batched: %s" % json.dumps(out["mixed_batched"]), file=sys.stderr, flush=True)
+        # one at a time (same mixed path) on a subset, then the plain FP64 path
+        sub = sorted(range(len(insts)), key=lambda q: insts[q].n)[:4]
+        t0 = time.perf_counter()
+        alone = []
+        for q in sub:
+            alone.append(ctxs[q].solve())
+        dt1 = time.perf_counter() - t0
+        out["mixed_one_at_a_time"] = {"solves_per_s": len(sub) / dt1, "instances": [insts[q].n for q in sub],
+                                      "same_as_batched": all(abs(a["obj"] - infos[q]["obj"]) <= 1e-9 * abs(a["obj"])
+                                                             and a["iters"] == infos[q]["iters"]
+                                                             for a, q in zip(alone, sub))}
+        print("one-at-a-time: %s" % json.dumps(out["mixed_one_at_a_time"]), file=sys.stderr, flush=True)
+        c64 = [_ctx_for(sdpgpu, insts[q], stream, P64, eps_abs=1e-4) for q in sub[:2]]
+        t0 = time.perf_counter()
+        r64 = [c.solve() for c in c64]
+        dt2 = time.perf_counter() - t0
+        out["fp64_one_at_a_time"] = {"solves_per_s": len(c64) / dt2, "instances": [insts[q].n for q in sub[:2]],
+                                     "rel_obj_vs_mixed": [abs(a["obj"] - infos[q]["obj"]) / abs(a["obj"])
+                                                          for a, q in zip(r64, sub[:2])]}
+        out["n_range"] = [min(i.n for i in insts), max(i.n for i in insts)]
+    elif args.workload == "serve":
+        reqs = gen.workload_serving(args.count, maxcut_n=(100, 1000), theta_n=(100, 600))
+        kw = dict(eps_abs=1e-4, tol_coef=0.1, precision=PMX)
+        srv = sdpgpu.Server(budget_bytes=64 << 30, max_slots=32, iters_per_step=40, stream=stream, **kw)
+        ctxs, tickets, arrive, done_t = {}, {}, {}, {}
+        t0 = time.perf_counter()
+        pending = list(enumerate(reqs))
+        while pending or len(done_t) < len(reqs):
+            now = time.perf_counter() - t0
+            while pending and pending[0][1][0] <= now:
+                i, (ta, inst) = pending.pop(0)
+                extra = {"rho": 10.0} if inst.meta.get("family") == "theta" else {}
+                c = sdpgpu.Context(stream=stream, **kw, **extra).setup(inst)
+                ctxs[i] = c
+                tickets[i] = srv.submit(c)
+                arrive[i] = ta
+            a, q = srv.step()
+            now = time.perf_counter() - t0
+            for i, t in tickets.items():
+                if i in done_t:
+                    continue
+                rc, info = srv.poll(t)
+                if rc not in (sdpgpu.SDP_RUNNING, sdpgpu.SDP_QUEUED):
+                    done_t[i] = (now, rc, info)
+            steps_done = getattr(srv, "_steps", 0) + 1
+            srv._steps = steps_done
+            if steps_done % 25 == 0:
+                print("serve t=%.1fs active=%d queued=%d done=%d" % (now, a, q, len(done_t)), file=sys.stderr,
+                      flush=True)
+            if a == 0 and q == 0 and not pending:
+                break
+            if a == 0 and q == 0 and pending:
+                time.sleep(max(0.0, min(0.05, pending[0][1][0] - now)))
+        lat = np.array([done_t[i][0] - arrive[i] for i in done_t])
+        wall = time.perf_counter() - t0
+        st = {}
+        for i in done_t:
+            k = sdpgpu.status_str(done_t[i][1])
+            st[k] = st.get(k, 0) + 1
+        pinf_ok = sum(1 for i in done_t if reqs[i][1].meta.get("family") == "pinf"
+                      and done_t[i][1] == sdpgpu.SDP_PRIMAL_INFEASIBLE)
+        out.update({"requests": len(reqs), "solves_per_s": len(done_t) / wall, "p50_s": float(np.percentile(lat, 50)),
+                    "p99_s": float(np.percentile(lat, 99)), "statuses": st,
+                    "infeasible_detected": pinf_ok,
+                    "infeasible_total": sum(1 for r in reqs if r[1].meta.get("family") == "pinf"),
+                    "arrival_rate_per_s": 50.0, "wall_s": wall})
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.kernel == "product":
+        return run_product(args)
+    if args.workload != "sweep":
+        return run_admm(args)
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -276,14 +468,36 @@ def main():
                 "avg_launch_ms": prod["ms"] / max(prod["timed"], 1)}
     roof["share_of_step"] = {k: round(v["ms"] / max(total_ms, 1e-9), 4) for k, v in prof.items() if v["ms"] > 0}
     roof["dominant_family"] = dom[0]
+    # the plain FP64 GPU path on the same sweep (one step after one warm-up)
+    fp64_path = None
+    if args.prec != "fp64" and not args.no_fp64_path and rank == 0:
+        c64 = sdpgpu.Context(stream=stream, precision=sdpgpu.PREC_FP64)
+        t64 = [0.5e-6 * float(np.linalg.norm(m["W"])) / np.sqrt(2.0 * m["k"]) for m in mats]
+
+        def step64():
+            for q, (m, Wd, X0, V, out) in enumerate(dev):
+                V.copy_(X0)
+                c64.project_raw(m["n"], Wd.data_ptr(), out.data_ptr(), V.data_ptr(), m["k"], m["n"], t64[q], True)
+        step64()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        e0.record(stream)
+        step64()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        fp64_path = {"value": len(mats) / (ms64 / 1000.0), "unit": "projections/s", "ms_per_step": ms64,
+                     "steps": 1, "note": "same sweep, FP64 products/Gram/Rayleigh-Ritz on CUDA cores, tol 0.5e-6"}
+        del c64
     # end to end through the C ABI with host buffers (H2D W + V, D2H result + V)
     e2e = None
     if not args.no_e2e and rank == 0:
         h2d = d2h = 0
         t0 = time.perf_counter()
         for _ in range(max(1, args.steps)):
-            for m, _, _, _, _ in dev:
-                P, Vout, info = ctx.project_psd(m["W"], m["X0"], tol=0.0, mcap=m["n"])
+            for q, (m, _, _, _, _) in enumerate(dev):
+                P, Vout, info = ctx.project_psd(m["W"], m["X0"], tol=tols[q], mcap=m["n"])
                 h2d += m["n"] * m["n"] * 8 + m["X0"].size * 8
                 d2h += m["n"] * m["n"] * 8 + Vout.size * 8
         dt = time.perf_counter() - t0
@@ -304,6 +518,8 @@ def main():
                            "precision": args.prec, "l2": "flushed between steps (256 MiB write)",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "fp64_path": fp64_path,
+                "speedup_vs_fp64_path": (value / fp64_path["value"]) if fp64_path else None,
                 "clocks": ck, "max_rel_err_vs_closed_form": max(errs),
                 "per_matrix": [{"n": m["n"], "k": m["k"], "ms": round(per_ms[q], 3), "rel_err": errs[q],
                                 "rr_steps": last_infos[q]["steps"], "m": last_infos[q]["m"],

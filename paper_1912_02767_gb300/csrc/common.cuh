@@ -120,6 +120,8 @@ struct Inst {
 // State of a grid-wide barrier and of the cooperative kernels using it.
 struct GridBar {
   unsigned count, gen;
+  unsigned top;        // groups arrived (two-level barrier)
+  unsigned grp[64];    // CTAs arrived per group of 16
   int err;     // a barrier wait gave up (bounded spin)
   int fail;    // Cholesky breakdown column (1-based), 0 if none
   int sweeps;  // Jacobi sweeps done

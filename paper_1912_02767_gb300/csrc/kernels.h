@@ -40,10 +40,14 @@ __global__ void k_gram_reduce(const GemmJob* jobs, WorkMap wm, int symmetrize);
 template <typename T>
 __global__ void k_rayleigh_ritz(Inst* insts, const int* list);
 template <typename T>
-__global__ void k_rr_smem(Inst* insts, const int* list);
-// largest trial subspace k_rr_smem<T> holds (2 p^2 elements of T <= 200 KiB)
+__global__ void k_rr_smem(Inst* insts, const int* list, int u_global);
+// largest trial subspace k_rr_smem<T> holds with both p x p workspaces in
+// shared memory (2 p^2 elements of T <= 200 KiB), and with one of them
+// (p^2 elements <= 205 KiB; the other in global memory)
 constexpr int kRRSmemMaxF32 = 160;
 constexpr int kRRSmemMaxF64 = 112;
+constexpr int kRRSmem1MaxF32 = 226;
+constexpr int kRRSmem1MaxF64 = 160;
 __global__ void k_resid(Inst* insts, WorkMap wm);
 __global__ void k_resid_finish(Inst* insts, const int* list, int last_allowed);
 __global__ void k_compact(Inst* insts, WorkMap wm);
@@ -72,6 +76,10 @@ __global__ void k_fro2_det(Inst* insts, const int* list);
 __global__ void k_fro2_mat(const double* A, int ld, int rows, int cols, double* dst);
 __global__ void k_seed_block(Inst* insts, WorkMap wm);
 __global__ void k_copy_cols(const double* src, int lds, double* dst, int ldd, int rows, int cols, double scale);
+
+// bj_eig.cu (host driver): block Jacobi, returns sweeps or -1
+int block_jacobi(cudaStream_t s, double* H, int ldh, double* U, int ldu, int p, bool f32, double eps,
+                 const double* fro2_dev, int max_sweeps, double* Q, double* offp, double* offh);
 
 // tc_gemm.cu (host wrappers)
 int tc_wprod(cudaStream_t s, const void* whi, const void* wlo, int ldw, const void* bhi, const void* blo, int ldb,

@@ -575,13 +575,17 @@ namespace sdpg {
 // Jacobi rounds.  Capacity: 2 p^2 elements of T in shared memory.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(1024) k_rr_smem(Inst* insts, const int* list) {
+__global__ void __launch_bounds__(1024) k_rr_smem(Inst* insts, const int* list, int u_global) {
   const Inst& I = insts[list[blockIdx.x]];
   Ctl* ctl = I.ctl;
   const int p = ctl->p, keep = ctl->keep;
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* A = (T*)smraw;      // p x p
-  T* B = A + p * p;      // p x p
+  // the two p x p workspaces (A: G -> L -> H, B: L^{-1} -> U): both in
+  // shared memory (u_global = 0), B in the instance's global scratch
+  // (u_global = 1), or both there (u_global = 2); global scratch stays
+  // L2-resident
+  T* A = u_global == 2 ? (T*)I.gpart : (T*)smraw;
+  T* B = u_global ? (T*)I.U : A + p * p;
   __shared__ T cs[2][160];
   __shared__ short pa[160], pb[160];
   __shared__ int ord[320];
@@ -749,6 +753,6 @@ __global__ void __launch_bounds__(1024) k_rr_smem(Inst* insts, const int* list) 
   }
 }
 
-template __global__ void k_rr_smem<double>(Inst*, const int*);
-template __global__ void k_rr_smem<float>(Inst*, const int*);
+template __global__ void k_rr_smem<double>(Inst*, const int*, int);
+template __global__ void k_rr_smem<float>(Inst*, const int*, int);
 }  // namespace sdpg

@@ -16,27 +16,37 @@
 namespace sdpg {
 
 __device__ __forceinline__ bool gbar(GridBar* b) {
+  // two-level arrival: CTAs count in groups of 16, the last of each group
+  // counts at the top, the last group bumps the generation everybody waits on
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned* vgen = &b->gen;
-    unsigned g = *vgen;
+    const unsigned nb = gridDim.x, g = blockIdx.x >> 4, ng = (nb + 15) >> 4;
+    const unsigned gs = (g + 1 < ng) ? 16u : nb - 16u * g;
+    unsigned gen0 = *vgen;
     __threadfence();
-    unsigned prev = atomicAdd(&b->count, 1u);
     ok = 1;
-    if (prev == gridDim.x - 1) {
-      atomicExch(&b->count, 0u);
+    bool last = false;
+    if (atomicAdd(&b->grp[g], 1u) == gs - 1) {
+      atomicExch(&b->grp[g], 0u);
       __threadfence();
-      atomicAdd(&b->gen, 1u);
-    } else {
+      if (atomicAdd(&b->top, 1u) == ng - 1) {
+        atomicExch(&b->top, 0u);
+        __threadfence();
+        atomicAdd(&b->gen, 1u);
+        last = true;
+      }
+    }
+    if (!last) {
       unsigned long long spins = 0;
-      while (*vgen == g) {
+      while (*vgen == gen0) {
         if (++spins > (1ull << 24)) {
           atomicExch(&b->err, 1);
           ok = 0;
           break;
         }
-        __nanosleep(64);
+        __nanosleep(32);
       }
     }
     if (*(volatile int*)&b->err) ok = 0;
@@ -52,7 +62,7 @@ __device__ __forceinline__ bool gbar(GridBar* b) {
 // (Gram of unit-norm columns) reports breakdown in b->fail (1-based col).
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_chol_inv_coop(double* G, double* Linv, int p, double piv_min, GridBar* b) {
+__global__ void __launch_bounds__(1024) k_chol_inv_coop(double* G, double* Linv, int p, double piv_min, GridBar* b) {
   __shared__ T Lkk[32][33];
   __shared__ int fail;
   const int nb = (p + 31) / 32;
@@ -195,7 +205,7 @@ __device__ __forceinline__ void rr_pair2(int r, int k, int np, int* a, int* b) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_jacobi_coop(double* H, double* H2, int ldh, double* U, int ldu, int p,
+__global__ void __launch_bounds__(1024) k_jacobi_coop(double* H, double* H2, int ldh, double* U, int ldu, int p,
                                                      double rel, double abs_eps, int max_sweeps, const double* fro2,
                                                      GridBar* b) {
   // per round: every CTA computes the round's P2 rotations into shared
