@@ -307,9 +307,9 @@ def run_admm(args):
                                                           for a, q in zip(r64, sub[:2])]}
         out["n_range"] = [min(i.n for i in insts), max(i.n for i in insts)]
     elif args.workload == "serve":
-        reqs = gen.workload_serving(args.count, maxcut_n=(100, 1000), theta_n=(100, 600))
+        reqs = gen.workload_serving(args.count, maxcut_n=(100, 600), theta_n=(100, 300))
         kw = dict(eps_abs=1e-4, tol_coef=0.1, precision=PMX)
-        srv = sdpgpu.Server(budget_bytes=64 << 30, max_slots=32, iters_per_step=40, stream=stream, **kw)
+        srv = sdpgpu.Server(budget_bytes=64 << 30, max_slots=32, iters_per_step=100, stream=stream, **kw)
         ctxs, tickets, arrive, done_t = {}, {}, {}, {}
         t0 = time.perf_counter()
         pending = list(enumerate(reqs))
@@ -332,7 +332,7 @@ def run_admm(args):
                     done_t[i] = (now, rc, info)
             steps_done = getattr(srv, "_steps", 0) + 1
             srv._steps = steps_done
-            if steps_done % 25 == 0:
+            if steps_done % 5 == 0:
                 print("serve t=%.1fs active=%d queued=%d done=%d" % (now, a, q, len(done_t)), file=sys.stderr,
                       flush=True)
             if a == 0 and q == 0 and not pending:

@@ -38,12 +38,12 @@ __device__ __forceinline__ int bj_bsize(int I, int nb, int p) {
 // One CTA per pair: load the submatrix, record its off-diagonal mass,
 // diagonalise it, store Q (BJ_S x BJ_S, column-major) for the pair.
 template <typename T>
-__global__ void __launch_bounds__(256) k_bj_sub(const double* H, int ldh, int p, int round, double* Q, double* offp) {
+__global__ void __launch_bounds__(512) k_bj_sub(const double* H, int ldh, int p, int round, double* Q, double* offp) {
   __shared__ T S[BJ_S][BJ_S + 1];
   __shared__ T V[BJ_S][BJ_S + 1];
   __shared__ T cs[2][BJ_S / 2];
   __shared__ int pa[BJ_S / 2], pb[BJ_S / 2];
-  __shared__ double red[8];
+  __shared__ double red[16];
   __shared__ int rotated;
   const int nb = (p + BJ_B - 1) / BJ_B, np = nb + (nb & 1);
   const int k = blockIdx.x;
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(256) k_bj_sub(const double* H, int ldh, int p,
     off += __shfl_down_sync(0xffffffffu, off, o);
     all += __shfl_down_sync(0xffffffffu, all, o);
   }
-  __shared__ double red2[8];
+  __shared__ double red2[16];
   __shared__ double sthr;
   if ((tid & 31) == 0) { red[tid >> 5] = off; red2[tid >> 5] = all; }
   __syncthreads();
@@ -81,9 +81,11 @@ __global__ void __launch_bounds__(256) k_bj_sub(const double* H, int ldh, int p,
     sthr = 16.0 * (sizeof(T) == 4 ? 6e-8 : 1.1e-16) * sqrt(a) / (double)(sz > 0 ? sz : 1);
   }
   __syncthreads();
-  // cyclic Jacobi on the sz x sz block to full convergence
+  // cyclic Jacobi on the sz x sz block: two sweeps (relaxed block Jacobi:
+  // the outer sweeps finish what the inner ones leave, at a fraction of the
+  // cost of diagonalising every subproblem to rounding level)
   const int snp = sz + (sz & 1), P2 = snp / 2;
-  for (int sweep = 0; sweep < 12 && sz >= 2; ++sweep) {
+  for (int sweep = 0; sweep < 2 && sz >= 2; ++sweep) {
     if (tid == 0) rotated = 0;
     __syncthreads();
     for (int r = 0; r < snp - 1; ++r) {
@@ -228,7 +230,7 @@ int block_jacobi(cudaStream_t s, double* H, int ldh, double* U, int ldu, int p, 
   for (; sweep < max_sweeps; ++sweep) {
     double off = 0.0;
     for (int r = 0; r < np - 1; ++r) {
-      k_bj_sub<float><<<npairs, 256, 0, s>>>(H, ldh, p, r, Q, offp + (size_t)r * npairs);
+      k_bj_sub<float><<<npairs, 512, 0, s>>>(H, ldh, p, r, Q, offp + (size_t)r * npairs);
       k_bj_rows<float><<<dim3(npairs, tiles), 256, 0, s>>>(H, ldh, p, r, Q);
       k_bj_cols<float><<<dim3(npairs, tiles, 2), 256, 0, s>>>(H, ldh, U, ldu, p, r, Q);
     }

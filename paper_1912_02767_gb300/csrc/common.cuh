@@ -26,6 +26,17 @@ __device__ __forceinline__ bool jacobi_rotates(double hab, double haa, double hb
   return fabs(hab) > (t > abs_thr ? t : abs_thr);
 }
 
+// Strict total order for the rank sort of Ritz values / eigenvalues: NaN
+// sorts below every number (it is never among the selected top values) and
+// ties break by index, so the ranks of p values always form a permutation of
+// 0..p-1 and every slot of the order array is written exactly once.
+__device__ __forceinline__ bool rank_before(double lj, int j, double li, int i) {
+  const bool nj = lj != lj, ni = li != li;
+  if (nj != ni) return nj;
+  if (!nj && lj != li) return lj < li;
+  return j < i;
+}
+
 // Per-instance control block (device memory, read back by the host).
 struct Ctl {
   int mode;      // projection mode of the current ADMM iteration

@@ -179,7 +179,7 @@ __global__ void k_jac_sort(Inst* insts, const int* list) {
     int rank = 0;
     for (int j = 0; j < n; ++j) {
       double lj = I.E[idx2(j, j, ld)];
-      rank += (lj < li) || (lj == li && j < i);
+      rank += rank_before((double)lj, j, (double)li, i);
     }
     I.eord[rank] = i;
     if (li > 0.0) atomicAdd(&np, 1);

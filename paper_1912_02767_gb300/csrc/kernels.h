@@ -40,14 +40,21 @@ __global__ void k_gram_reduce(const GemmJob* jobs, WorkMap wm, int symmetrize);
 template <typename T>
 __global__ void k_rayleigh_ritz(Inst* insts, const int* list);
 template <typename T>
-__global__ void k_rr_smem(Inst* insts, const int* list, int u_global);
+__global__ void k_rr_smem(Inst* insts, const int* list, int u_global, int p_launch);
 // largest trial subspace k_rr_smem<T> holds with both p x p workspaces in
 // shared memory (2 p^2 elements of T <= 200 KiB), and with one of them
 // (p^2 elements <= 205 KiB; the other in global memory)
 constexpr int kRRSmemMaxF32 = 160;
 constexpr int kRRSmemMaxF64 = 112;
-constexpr int kRRSmem1MaxF32 = 226;
-constexpr int kRRSmem1MaxF64 = 160;
+constexpr int kRRSmem1MaxF32 = 224;
+constexpr int kRRSmem1MaxF64 = 156;
+constexpr int kRRGlobalMax = 1024;  // one-CTA Rayleigh-Ritz with both workspaces in global memory
+// shared-memory bytes of k_rr_smem's rotation table + sort order for width p
+__host__ __device__ inline size_t rr_table_bytes(int p, int tsize) {
+  const int P2 = (p + 1) / 2;
+  size_t b = (size_t)2 * P2 * tsize + (size_t)2 * P2 * sizeof(int) + (size_t)p * sizeof(int);
+  return (b + 15) / 16 * 16;
+}
 __global__ void k_resid(Inst* insts, WorkMap wm);
 __global__ void k_resid_finish(Inst* insts, const int* list, int last_allowed);
 __global__ void k_compact(Inst* insts, WorkMap wm);
@@ -60,7 +67,7 @@ __global__ void k_chol_inv_coop(double* G, double* Linv, int p, double piv_min, 
 template <typename T>
 __global__ void k_jacobi_coop(double* H, double* H2, int ldh, double* U, int ldu, int p, double rel, double abs_eps,
                               int max_sweeps, const double* fro2, GridBar* b);
-__global__ void k_diag_rank(const double* H, int ldh, int p, int* ord);
+__global__ void k_diag_rank(const double* H, int ldh, int p, int* ord, int* fail);
 __global__ void k_select_top(const double* H, int ldh, const double* U, int ldu, int p, int keep, const int* ord,
                              double* Usel, double* theta, int* npos);
 __global__ void k_rr_large_finish(Ctl* ctl, const GridBar* b);

@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(1024) k_rayleigh_ritz(Inst* insts, const int* 
     int rank = 0;
     for (int j = 0; j < p; ++j) {
       double lj = H[idx2(j, j, p)];
-      rank += (lj < li) || (lj == li && j < i);
+      rank += rank_before((double)lj, j, (double)li, i);
     }
     ord[rank] = i;
   }
@@ -334,10 +334,13 @@ __global__ void __launch_bounds__(1024) k_rayleigh_ritz(Inst* insts, const int* 
   }
   for (int j = threadIdx.x; j < keep; j += blockDim.x) I.theta[j] = H[idx2(ord[p - keep + j], ord[p - keep + j], p)];
   if (threadIdx.x == 0) {
-    int np = 0;
-    for (int j = 0; j < p; ++j) np += H[idx2(j, j, p)] > 0.0;
+    int np = 0, bad = 0;
+    for (int j = 0; j < p; ++j) {
+      np += H[idx2(j, j, p)] > 0.0;
+      bad |= !isfinite(H[idx2(j, j, p)]);
+    }
     ctl->npos_rr = np;
-    ctl->rr_fail = 0;
+    ctl->rr_fail = bad ? -3 : 0;  // non-finite Ritz values: breakdown
     ctl->sweeps += sw;
   }
 }
@@ -574,21 +577,33 @@ namespace sdpg {
 // Coef = L^{-T} U_top -- without global-memory round trips inside the
 // Jacobi rounds.  Capacity: 2 p^2 elements of T in shared memory.
 // ---------------------------------------------------------------------------
+// Dynamic shared memory: [A: p*p T][B: p*p T] (as the mode keeps them)
+// followed by the per-round rotation table and the sort order
+// (rr_table_bytes in kernels.h).
 template <typename T>
-__global__ void __launch_bounds__(1024) k_rr_smem(Inst* insts, const int* list, int u_global) {
+__global__ void __launch_bounds__(1024) k_rr_smem(Inst* insts, const int* list, int u_global, int p_launch) {
   const Inst& I = insts[list[blockIdx.x]];
   Ctl* ctl = I.ctl;
   const int p = ctl->p, keep = ctl->keep;
+  if (p < 1 || p > p_launch || p > kRRGlobalMax || keep < 1 || keep > p) {  // launch sized for another width: refuse, no access
+    if (threadIdx.x == 0) ctl->rr_fail = -2;
+    return;
+  }
   extern __shared__ __align__(16) unsigned char smraw[];
   // the two p x p workspaces (A: G -> L -> H, B: L^{-1} -> U): both in
   // shared memory (u_global = 0), B in the instance's global scratch
   // (u_global = 1), or both there (u_global = 2); global scratch stays
   // L2-resident
+  const int in_smem = u_global == 0 ? 2 : u_global == 1 ? 1 : 0;
   T* A = u_global == 2 ? (T*)I.gpart : (T*)smraw;
   T* B = u_global ? (T*)I.U : A + p * p;
-  __shared__ T cs[2][160];
-  __shared__ short pa[160], pb[160];
-  __shared__ int ord[320];
+  unsigned char* tab = smraw + (size_t)in_smem * p * p * sizeof(T);
+  const int P2max = (p + 1) / 2;
+  T* cs0 = (T*)tab;
+  T* cs1 = cs0 + P2max;
+  int* pa = (int*)(cs1 + P2max);
+  int* pb = pa + P2max;
+  int* ord = pb + P2max;
   __shared__ int fail, rotated;
   __shared__ double red[32];
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -683,15 +698,15 @@ __global__ void __launch_bounds__(1024) k_rr_smem(Inst* insts, const int* list, 
             rotated = 1;
           }
         }
-        cs[0][k] = c; cs[1][k] = s; pa[k] = (short)a; pb[k] = (short)b;
+        cs0[k] = c; cs1[k] = s; pa[k] = a; pb[k] = b;
       }
       __syncthreads();
       for (int e = tid; e < P2 * P2; e += nt) {
         int ki = e % P2, kj = e / P2;
-        T si = cs[1][ki], sj = cs[1][kj];
+        T si = cs1[ki], sj = cs1[kj];
         if (si == (T)0 && sj == (T)0) continue;
         int ai = pa[ki], bi = pb[ki], aj = pa[kj], bj = pb[kj];
-        T ci = cs[0][ki], cj = cs[0][kj];
+        T ci = cs0[ki], cj = cs0[kj];
         bool vai = ai < p, vbi = bi < p, vaj = aj < p, vbj = bj < p;
         T haa = (vai && vaj) ? A[ai + aj * p] : (T)0;
         T hab = (vai && vbj) ? A[ai + bj * p] : (T)0;
@@ -709,11 +724,11 @@ __global__ void __launch_bounds__(1024) k_rr_smem(Inst* insts, const int* list, 
       }
       for (int e = tid; e < p * P2; e += nt) {
         int row = e % p, k = e / p;
-        T s = cs[1][k];
+        T s = cs1[k];
         if (s == (T)0) continue;
         int a = pa[k], b = pb[k];
         if (a >= p || b >= p) continue;
-        T c = cs[0][k];
+        T c = cs0[k];
         T ua = B[row + a * p], ub = B[row + b * p];
         B[row + a * p] = c * ua - s * ub;
         B[row + b * p] = s * ua + c * ub;
@@ -730,7 +745,7 @@ __global__ void __launch_bounds__(1024) k_rr_smem(Inst* insts, const int* list, 
     int rank = 0;
     for (int j = 0; j < p; ++j) {
       T lj = A[j + j * p];
-      rank += (lj < li) || (lj == li && j < i);
+      rank += rank_before((double)lj, j, (double)li, i);
     }
     ord[rank] = i;
   }
@@ -745,14 +760,17 @@ __global__ void __launch_bounds__(1024) k_rr_smem(Inst* insts, const int* list, 
   }
   for (int j = tid; j < keep; j += nt) I.theta[j] = (double)A[ord[p - keep + j] * (p + 1)];
   if (tid == 0) {
-    int c = 0;
-    for (int j = 0; j < p; ++j) c += A[j + j * p] > (T)0;
+    int c = 0, bad = 0;
+    for (int j = 0; j < p; ++j) {
+      c += A[j + j * p] > (T)0;
+      bad |= !isfinite((double)A[j + j * p]);
+    }
     ctl->npos_rr = c;
-    ctl->rr_fail = 0;
+    ctl->rr_fail = bad ? -3 : 0;  // non-finite Ritz values: breakdown
     ctl->sweeps += sweeps;
   }
 }
 
-template __global__ void k_rr_smem<double>(Inst*, const int*, int);
-template __global__ void k_rr_smem<float>(Inst*, const int*, int);
+template __global__ void k_rr_smem<double>(Inst*, const int*, int, int);
+template __global__ void k_rr_smem<float>(Inst*, const int*, int, int);
 }  // namespace sdpg

@@ -1,6 +1,8 @@
 // prof.h -- launch counting and CUDA-event timing per kernel family.
 #pragma once
 #include <cuda_runtime.h>
+#include <stdio.h>
+#include <stdlib.h>
 
 #include <vector>
 
@@ -52,8 +54,10 @@ struct ProfScope {
   int fam;
   cudaStream_t s;
   double fl, by;
+  const char* name;
   cudaEvent_t a = nullptr;
-  ProfScope(int f, cudaStream_t st, double flops = 0, double bytes = 0) : fam(f), s(st), fl(flops), by(bytes) {
+  ProfScope(int f, cudaStream_t st, double flops = 0, double bytes = 0, const char* nm = "")
+      : fam(f), s(st), fl(flops), by(bytes), name(nm) {
     Prof& P = prof();
     P.launches[fam]++;
     P.flops[fam] += fl;
@@ -65,6 +69,13 @@ struct ProfScope {
   }
   ~ProfScope() {
     Prof& P = prof();
+    static const int dbg = getenv("SDP_DEBUG") ? atoi(getenv("SDP_DEBUG")) : 0;
+    if (dbg) {  // debugging aid: name the kernel family of the first failing launch
+      cudaError_t e = cudaStreamSynchronize(s);
+      if (e == cudaSuccess) e = cudaGetLastError();
+      if (e != cudaSuccess) fprintf(stderr, "[sdpgpu] CUDA error after a launch of family %d (%s): %s\n", fam,
+                                    name, cudaGetErrorString(e));
+    }
     if (a) {
       cudaEvent_t b = P.get();
       cudaEventRecord(b, s);

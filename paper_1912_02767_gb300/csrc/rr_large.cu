@@ -297,14 +297,15 @@ __global__ void __launch_bounds__(1024) k_jacobi_coop(double* H, double* H2, int
 
 // Ascending order of the diagonal of H (rank sort), the top `keep` values,
 // positive count; grid over i.
-__global__ void k_diag_rank(const double* H, int ldh, int p, int* ord) {
+__global__ void k_diag_rank(const double* H, int ldh, int p, int* ord, int* fail) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= p) return;
   double li = H[idx2(i, i, ldh)];
+  if (!isfinite(li)) atomicCAS(fail, 0, -3);  // non-finite Ritz value: breakdown
   int rank = 0;
   for (int j = 0; j < p; ++j) {
     double lj = H[idx2(j, j, ldh)];
-    rank += (lj < li) || (lj == li && j < i);
+    rank += rank_before((double)lj, j, (double)li, i);
   }
   ord[rank] = i;
 }
