@@ -44,12 +44,28 @@ def parse():
     ap.add_argument("--workload", default="sweep", choices=["sweep", "maxcut64", "theta500", "batch", "serve"],
                     help="sweep: the projection sweep (the bench line); the others time ADMM solves")
     ap.add_argument("--count", type=int, default=64, help="instances (batch) or requests (serve)")
+    ap.add_argument("--rr", type=int, default=0, choices=[0, 1],
+                    help="Rayleigh-Ritz eigensolver: 0 tridiagonal where it fits (default), 1 Jacobi")
     ap.add_argument("--kernel", default=None, choices=[None, "product"],
                     help="time one kernel alone: 'product' = W B on the tensor cores (sdp_block_product)")
     ap.add_argument("--n", type=int, default=6144)
     ap.add_argument("--k", type=int, default=256)
     ap.add_argument("--iters", type=int, default=20)
     return ap.parse_args()
+
+
+def _family_ms(sdpgpu, fn):
+    """Device time per kernel family (CUDA events around each launch) of one
+    more call of `fn`; the events serialise launches, so this is a breakdown,
+    not a throughput figure."""
+    sdpgpu.prof_reset()
+    sdpgpu.prof_enable(True)
+    try:
+        fn()
+    finally:
+        sdpgpu.prof_enable(False)
+    prof = sdpgpu.prof_get()
+    return {k: {"ms": round(v["ms"], 3), "launches": v["launches"]} for k, v in prof.items() if v["launches"]}
 
 
 def run_product(args):
@@ -254,7 +270,7 @@ def run_admm(args):
         t_or = time.perf_counter() - t0
         for name, kw in [("fp64", dict(precision=P64)), ("mixed", dict(precision=PMX)),
                          ("exact_eig_fp64", dict(precision=P64, exact_only=1))]:
-            c = sdpgpu.Context(stream=stream, eps_abs=1e-4, **kw).setup(inst)
+            c = sdpgpu.Context(stream=stream, eps_abs=1e-4, rr_method=args.rr, **kw).setup(inst)
             c.solve()
             reps = max(1, args.steps)
             t0 = time.perf_counter()
@@ -263,12 +279,13 @@ def run_admm(args):
             dt = (time.perf_counter() - t0) / reps
             out[name] = {"solves_per_s": 1.0 / dt, "ms": 1000 * dt, "iters": r["iters"], "status": r["status_name"],
                          "obj": r["obj"], "rel_obj_err_vs_oracle": abs(r["obj"] - ref["obj"]) / abs(ref["obj"]),
-                         "n_lobpcg": r["n_lobpcg"], "n_exact": r["n_exact"], "lobpcg_steps": r["lobpcg_steps"]}
+                         "n_lobpcg": r["n_lobpcg"], "n_exact": r["n_exact"], "lobpcg_steps": r["lobpcg_steps"],
+                         "device_ms_by_family": _family_ms(sdpgpu, c.solve)}
         out["oracle_exact_cpu"] = {"solves_per_s": 1.0 / t_or, "iters": ref["iters"], "obj": ref["obj"], "cores": 1}
     elif args.workload == "theta500":
         inst = gen.workload_theta500(0)
         for name, prec in [("mixed", PMX), ("fp64", P64)]:
-            c = sdpgpu.Context(stream=stream, precision=prec, eps_abs=1e-4, rho=10.0).setup(inst)
+            c = sdpgpu.Context(stream=stream, precision=prec, eps_abs=1e-4, rho=10.0, rr_method=args.rr).setup(inst)
             t0 = time.perf_counter()
             r = c.solve()
             dt = time.perf_counter() - t0
@@ -277,7 +294,7 @@ def run_admm(args):
                          "n_lobpcg": r["n_lobpcg"], "n_exact": r["n_exact"]}
     elif args.workload == "batch":
         insts = gen.workload_batch(args.count)
-        ctxs = [_ctx_for(sdpgpu, i, stream, PMX, eps_abs=1e-4) for i in insts]
+        ctxs = [_ctx_for(sdpgpu, i, stream, PMX, eps_abs=1e-4, rr_method=args.rr) for i in insts]
         t0 = time.perf_counter()
         infos = sdpgpu.batch_solve(ctxs)
         dt = time.perf_counter() - t0
@@ -298,7 +315,7 @@ def run_admm(args):
                                                              and a["iters"] == infos[q]["iters"]
                                                              for a, q in zip(alone, sub))}
         print("one-at-a-time: %s" % json.dumps(out["mixed_one_at_a_time"]), file=sys.stderr, flush=True)
-        c64 = [_ctx_for(sdpgpu, insts[q], stream, P64, eps_abs=1e-4) for q in sub[:2]]
+        c64 = [_ctx_for(sdpgpu, insts[q], stream, P64, eps_abs=1e-4, rr_method=args.rr) for q in sub[:2]]
         t0 = time.perf_counter()
         r64 = [c.solve() for c in c64]
         dt2 = time.perf_counter() - t0
@@ -318,7 +335,7 @@ def run_admm(args):
             while pending and pending[0][1][0] <= now:
                 i, (ta, inst) = pending.pop(0)
                 extra = {"rho": 10.0} if inst.meta.get("family") == "theta" else {}
-                c = sdpgpu.Context(stream=stream, **kw, **extra).setup(inst)
+                c = sdpgpu.Context(stream=stream, rr_method=args.rr, **kw, **extra).setup(inst)
                 ctxs[i] = c
                 tickets[i] = srv.submit(c)
                 arrive[i] = ta
@@ -377,7 +394,7 @@ def main():
     sdpgpu.load()
     prec = sdpgpu.PREC_FP64 if args.prec == "fp64" else sdpgpu.PREC_BF16X3
     stream = torch.cuda.current_stream()
-    ctx = sdpgpu.Context(stream=stream, precision=prec)
+    ctx = sdpgpu.Context(stream=stream, precision=prec, rr_method=args.rr)
     mats = make_mats(args)
     dev = []
     for m in mats:
@@ -471,7 +488,7 @@ def main():
     # the plain FP64 GPU path on the same sweep (one step after one warm-up)
     fp64_path = None
     if args.prec != "fp64" and not args.no_fp64_path and rank == 0:
-        c64 = sdpgpu.Context(stream=stream, precision=sdpgpu.PREC_FP64)
+        c64 = sdpgpu.Context(stream=stream, precision=sdpgpu.PREC_FP64, rr_method=args.rr)
         t64 = [0.5e-6 * float(np.linalg.norm(m["W"])) / np.sqrt(2.0 * m["k"]) for m in mats]
 
         def step64():

@@ -80,6 +80,10 @@ typedef struct {
   double expand_frac;  /* expansion block b = ceil(expand_frac*n) (Section 4) default 1/50 */
   double mode_frac;    /* positive/negative mode threshold (Section 5)     default 1/3   */
   unsigned long long seed; /* Philox key for the random expansion columns  default 0     */
+  int rr_method;       /* Rayleigh-Ritz eigensolver: 0 tridiagonal reduction where the   */
+                       /* p x p matrix fits one CTA's shared memory, Jacobi above;        */
+                       /* 1 Jacobi at every width (comparator)            default 0     */
+  int reserved;        /* must be 0                                                     */
 } sdp_settings;
 
 typedef struct {

@@ -55,6 +55,19 @@ __host__ __device__ inline size_t rr_table_bytes(int p, int tsize) {
   size_t b = (size_t)2 * P2 * tsize + (size_t)2 * P2 * sizeof(int) + (size_t)p * sizeof(int);
   return (b + 15) / 16 * 16;
 }
+// rr_tri.cu: Rayleigh-Ritz by tridiagonal reduction, one CTA (1024 threads)
+// per instance; zsm = 1 keeps the p x keep Ritz block in shared memory
+template <typename T>
+__global__ void k_rr_tri(Inst* insts, const int* list, int zsm, unsigned smem_launch);
+// dynamic shared memory of k_rr_tri<T> for width p, with the Ritz block of
+// zk columns in shared memory (zk = keep) or in global memory (zk = 0)
+__host__ __device__ inline size_t rr_tri_smem_bytes(int p, int zk, int tsize) {
+  return ((size_t)p * (size_t)(p | 1) + 11 * (size_t)p + 1024 + (size_t)p * (size_t)zk) * (size_t)tsize;
+}
+constexpr size_t kRRTriSmemMax = 231936;  // 227 KiB per CTA less the kernel's static shared memory
+// threads of a k_rr_tri CTA for widths up to p (p <= threads): fewer warps
+// per barrier for narrow subspaces, all 32 for wide ones
+inline int rr_tri_threads(int p) { return p <= 32 ? 128 : (p <= 64 ? 256 : (p <= 128 ? 512 : 1024)); }
 __global__ void k_resid(Inst* insts, WorkMap wm);
 __global__ void k_resid_finish(Inst* insts, const int* list, int last_allowed);
 __global__ void k_compact(Inst* insts, WorkMap wm);

@@ -125,3 +125,45 @@ def test_block_product_tensor_cores(sdp, n, k):
         got = out.cpu().numpy().T
         err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
         assert np.all(np.isfinite(got)) and err <= tol, (prec, err)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+@pytest.mark.parametrize("n,f", [(100, 0.2), (257, 0.03), (300, 0.3)])
+def test_rayleigh_ritz_methods_agree(sdp, n, f, prec):
+    """The Rayleigh-Ritz step by tridiagonal reduction (Householder, Sturm
+    bisection, inverse iteration) and by cyclic Jacobi both give the
+    projection of Eq. 2 at the precision's level, with the same rank."""
+    sp = gen.random_spectrum(n, f, np.random.default_rng(500 + n))
+    nW = np.linalg.norm(sp["W"])
+    ref = closed_form(sp)
+    p = sdp.PREC_FP64 if prec == "fp64" else sdp.PREC_BF16X3
+    tol = None if prec == "fp64" else 1e-5 * nW / np.sqrt(2 * sp["k"])
+    bound = TOL_FP64 if prec == "fp64" else 1e-4
+    out = []
+    for rm in (0, 1):
+        ctx = sdp.Context(precision=p, rr_method=rm)
+        P, V, info = ctx.project_psd(sp["W"], sp["X0"]) if tol is None else ctx.project_psd(sp["W"], sp["X0"], tol=tol)
+        assert np.linalg.norm(P - ref) / nW <= bound, (rm, np.linalg.norm(P - ref) / nW)
+        assert info["npos"] == sp["k"]
+        out.append(P)
+    assert np.linalg.norm(out[0] - out[1]) / nW <= 2 * bound
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_projection_repeated_eigenvalues(sdp, prec):
+    """Eigenvalues repeated exactly (multiplicities 8 and 4 among the
+    positives, 20 at -1): the Ritz block is any orthonormal basis of each
+    eigenspace and the projection is still exact."""
+    n = 160
+    rng = np.random.default_rng(21)
+    Q = gen.haar_orthogonal(n, rng)
+    lam = np.concatenate([np.full(8, 1.0), np.full(4, 0.5), np.full(20, -1.0), -rng.uniform(0.1, 0.9, n - 32)])
+    W = (Q * lam) @ Q.T
+    X0 = Q[:, :12] + 1e-3 * rng.standard_normal((n, 12))
+    ref = (Q[:, :12] * lam[:12]) @ Q[:, :12].T
+    p = sdp.PREC_FP64 if prec == "fp64" else sdp.PREC_BF16X3
+    ctx = sdp.Context(precision=p)
+    tol = 1e-10 if prec == "fp64" else 1e-5 * np.linalg.norm(W) / np.sqrt(24)
+    P, V, info = ctx.project_psd(W, X0, tol=tol)
+    assert info["npos"] == 12
+    assert np.linalg.norm(P - ref) / np.linalg.norm(W) <= (TOL_FP64 if prec == "fp64" else 1e-4)
