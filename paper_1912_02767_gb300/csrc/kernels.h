@@ -85,6 +85,20 @@ __global__ void k_select_top(const double* H, int ldh, const double* U, int ldu,
                              double* Usel, double* theta, int* npos);
 __global__ void k_rr_large_finish(Ctl* ctl, const GridBar* b);
 
+// rr_wide.cu (one wide subspace over the whole GPU, tridiagonal route)
+template <typename T>
+__global__ void k_trid_coop(const double* H, T* A, int p, int keep, double* vb, GridBar* b);
+template <typename TS, typename T>
+__global__ void k_trid_eig(double* vb, int p, int keep, int S, int refine, int final, double* theta, int* npos,
+                           const GridBar* b);
+template <typename T>
+__global__ void k_trid_shift(double* vb, int p, int keep, const GridBar* b);
+template <typename T>
+__global__ void k_trid_invit(double* vb, int p, int keep, double* Z, T* WS, const GridBar* b);
+template <typename T>
+__global__ void k_trid_backtr(const T* A, double* vb, int p, int keep, double* Y, int nv, const GridBar* b);
+constexpr int kTridBacktrNv = 16;  // vectors per CTA of k_trid_backtr (at most)
+
 // jacobi_kernels.cu (exact branch)
 __global__ void k_jac_init(Inst* insts, WorkMap wm, int negate);
 __global__ void k_jac_angles(Inst* insts, WorkMap wm, int round);

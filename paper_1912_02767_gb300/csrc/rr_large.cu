@@ -12,49 +12,10 @@
 // operation.
 #include "common.cuh"
 #include "kernels.h"
+#include "gridbar.cuh"
 
 namespace sdpg {
 
-__device__ __forceinline__ bool gbar(GridBar* b) {
-  // two-level arrival: CTAs count in groups of 16, the last of each group
-  // counts at the top, the last group bumps the generation everybody waits on
-  __shared__ int ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned* vgen = &b->gen;
-    const unsigned nb = gridDim.x, g = blockIdx.x >> 4, ng = (nb + 15) >> 4;
-    const unsigned gs = (g + 1 < ng) ? 16u : nb - 16u * g;
-    unsigned gen0 = *vgen;
-    __threadfence();
-    ok = 1;
-    bool last = false;
-    if (atomicAdd(&b->grp[g], 1u) == gs - 1) {
-      atomicExch(&b->grp[g], 0u);
-      __threadfence();
-      if (atomicAdd(&b->top, 1u) == ng - 1) {
-        atomicExch(&b->top, 0u);
-        __threadfence();
-        atomicAdd(&b->gen, 1u);
-        last = true;
-      }
-    }
-    if (!last) {
-      unsigned long long spins = 0;
-      while (*vgen == gen0) {
-        if (++spins > (1ull << 24)) {
-          atomicExch(&b->err, 1);
-          ok = 0;
-          break;
-        }
-        __nanosleep(32);
-      }
-    }
-    if (*(volatile int*)&b->err) ok = 0;
-    __threadfence();
-  }
-  __syncthreads();
-  return ok != 0;
-}
 
 // ---------------------------------------------------------------------------
 // Blocked Cholesky (32-column panels) and triangular inverse, in place on

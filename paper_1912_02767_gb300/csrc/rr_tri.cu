@@ -24,114 +24,11 @@
 // instance's global scratch U. L~ is kept in the scratch Linv and the
 // inverse-iteration factors in gpart (both L2-resident).
 #include "kernels.h"
+#include "tri_common.cuh"
 
 namespace sdpg {
 
-namespace {
-
-template <typename T>
-struct TriK;
-template <>
-struct TriK<float> {
-  static constexpr float piv_min = 1e-6f;           // Cholesky-QR breakdown (Gram of unit columns)
-  static constexpr float eps = 5.9604645e-08f;      // unit roundoff 2^-24
-  static constexpr float safmin = 1.17549435e-38f;  // smallest normal
-};
-template <>
-struct TriK<double> {
-  static constexpr double piv_min = 1e-12;
-  static constexpr double eps = 1.1102230246251565e-16;  // 2^-53
-  static constexpr double safmin = 2.2250738585072014e-308;
-};
-
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-template <typename T>
-__device__ __forceinline__ T warp_min(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-template <typename T>
-__device__ __forceinline__ T warp_max(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-
-// Number of eigenvalues of the symmetric tridiagonal (d, e) below x: the
-// count of negative pivots of the LDL^T factorization of T - x I (Sturm
-// sequence).  A pivot smaller than pivmin in magnitude is replaced by
-// -pivmin, which keeps the count monotone in x.
-template <typename T>
-__device__ __forceinline__ int sturm_below(const T* d, const T* e2, int p, T x, T pivmin) {
-  T q = d[0] - x;
-  if (fabs(q) < pivmin) q = -pivmin;
-  int c = q < (T)0;
-  for (int i = 1; i < p; ++i) {
-    q = (d[i] - x) - e2[i - 1] / q;
-    if (fabs(q) < pivmin) q = -pivmin;
-    c += q < (T)0;
-  }
-  return c;
-}
-
-// Start vector of inverse iteration: uniform in [-1, 1) from the Philox
-// stream keyed for this purpose (row i, vector q).
-template <typename T>
-__device__ __forceinline__ T start_value(int i, int q) {
-  uint32_t c[4] = {(uint32_t)i, (uint32_t)q, 0x52525452u, 0u};
-  philox4x32_10(c, 0x7452694Eu, 0x49544552u);
-  return (T)((double)c[0] * (1.0 / 2147483648.0) - 1.0);
-}
-
-// S-section search for eigenvalues p-keep .. p-1 (ascending) of the
-// tridiagonal (d, e2 = e^2): lane groups of S (a power of two <= 32) per
-// eigenvalue, each lane counting at one of S interior points per step, until
-// the bracket is narrower than tol.  refine = false: start from [lo0, hi0];
-// refine = true: start from lam[q] -/+ lo0 (checked by two counts, else the
-// whole scaled spectrum [-1.01, 1.01]).  Writes lam[q] (midpoint).
-template <typename TS, typename TL>
-__device__ void section_search(const TS* d, const TS* e2, int p, int keep, int S, TS tol, TS lo0, TS hi0, TS pivmin,
-                               TL* lam, bool refine) {
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
-  const int G = nt / S, g = tid / S, sl = tid % S;
-  const unsigned gbase = (unsigned)(lane & ~(S - 1));
-  const unsigned gmask = S == 32 ? 0xffffffffu : (((1u << S) - 1u) << gbase);
-  for (int q = g; q < keep; q += G) {  // lanes of a group share q: group-uniform
-    const int J = p - keep + q;
-    TS lo = lo0, hi = hi0;
-    if (refine) {
-      const TS c = (TS)lam[q];
-      lo = c - lo0;
-      hi = c + lo0;
-      const int clo = sturm_below(d, e2, p, lo, pivmin), chi = sturm_below(d, e2, p, hi, pivmin);
-      if (!(clo <= J && J < chi)) {
-        lo = (TS)-1.01;
-        hi = (TS)1.01;
-      }
-    }
-    for (int it = 0; it < 200 && hi - lo > tol; ++it) {
-      const TS step = (hi - lo) / (TS)(S + 1);
-      const int c = sturm_below(d, e2, p, lo + step * (TS)(sl + 1), pivmin);
-      unsigned b = __ballot_sync(gmask, c > J) >> gbase;
-      if (S < 32) b &= (1u << S) - 1u;
-      const int f = __ffs(b) - 1;  // first point above eigenvalue J (-1: none)
-      const TS nlo = f < 0 ? lo + step * (TS)S : (f == 0 ? lo : lo + step * (TS)f);
-      const TS nhi = f < 0 ? hi : lo + step * (TS)(f + 1);
-      if (nlo == lo && nhi == hi) break;  // no representable progress
-      lo = nlo;
-      hi = nhi;
-    }
-    if (sl == 0) lam[q] = (TL)((TS)0.5 * (lo + hi));
-  }
-}
-
-}  // namespace
+using namespace tri;
 
 template <typename T>
 __global__ void __launch_bounds__(1024) k_rr_tri(Inst* insts, const int* list, int zsm, unsigned smem_launch) {
@@ -175,7 +72,7 @@ __global__ void __launch_bounds__(1024) k_rr_tri(Inst* insts, const int* list, i
   __syncthreads();
   for (int j = 0; j < p; ++j) {
     const T djj = B[j + j * ldp];
-    if (!(djj > (T)TriK<T>::piv_min)) {
+    if (!(djj > (T)K<T>::piv_min)) {
       if (tid == 0) s_fail = j + 1;
       break;  // every thread reads the same pivot: uniform exit
     }
@@ -376,20 +273,21 @@ __global__ void __launch_bounds__(1024) k_rr_tri(Inst* insts, const int* list, i
     }
     int S2 = 32;
     while (S2 > 1 && S2 * keep > nt) S2 >>= 1;
-    const float tol32 = (dbl ? 32.0f : 4.0f) * TriK<float>::eps;
-    section_search<float>(db, eb, p, keep, S2, tol32, -1.01f, 1.01f, TriK<float>::safmin, lam, false);
+    const float tol32 = (dbl ? 32.0f : 4.0f) * K<float>::eps;
+    section_search<float>(db, eb, p, keep, S2, tid / S2, nt / S2, tol32, -1.01f, 1.01f, K<float>::safmin, lam,
+                          false);
     if (dbl) {
       __syncthreads();
       int S4 = 4;
       while (S4 > 1 && S4 * keep > nt) S4 >>= 1;
-      section_search<T>(d, e2, p, keep, S4, (T)4 * TriK<T>::eps, (T)(64.0f * TriK<float>::eps), (T)0,
-                        (T)TriK<T>::safmin, lam, true);
+      section_search<T>(d, e2, p, keep, S4, tid / S4, nt / S4, (T)4 * K<T>::eps, (T)(64.0f * K<float>::eps),
+                        (T)0, (T)K<T>::safmin, lam, true);
     }
-    if (tid == nt - 1) s_npos = p - sturm_below(d, e2, p, (T)0, (T)TriK<T>::safmin);
+    if (tid == nt - 1) s_npos = p - sturm_below(d, e2, p, (T)0, (T)K<T>::safmin);
   }
   __syncthreads();
   if (tid == 0) {  // shifts at least 10 eps apart, so that equal eigenvalues get distinct vectors
-    const T sep = (T)10 * TriK<T>::eps;
+    const T sep = (T)10 * K<T>::eps;
     T prev = lam[0];
     sig[0] = prev;
     for (int q = 1; q < keep; ++q) {
@@ -404,52 +302,7 @@ __global__ void __launch_bounds__(1024) k_rr_tri(Inst* insts, const int* list, i
   // ---- 6. inverse iteration, one thread per eigenvector: Gaussian
   // elimination with partial pivoting of T - sig I (U has two
   // superdiagonals), three solves from a random start
-  for (int q = tid; q < keep; q += nt) {
-    const T sg = sig[q], tiny = TriK<T>::eps;
-    for (int i = 0; i < p; ++i) Z[(size_t)i * keep + q] = start_value<T>(i, q);
-    for (int it = 0; it < 3; ++it) {
-      T a = d[0] - sg, bc = p > 1 ? e[0] : (T)0, zi = Z[q];
-      for (int i = 0; i + 1 < p; ++i) {
-        const T ei = e[i], an = d[i + 1] - sg, en = i + 2 < p ? e[i + 1] : (T)0;
-        const T zn = Z[(size_t)(i + 1) * keep + q];
-        T u0, u1, u2, zr;
-        if (fabs(a) >= fabs(ei)) {  // pivot on the active row
-          if (a == (T)0) a = tiny;
-          const T f = ei / a;
-          u0 = a; u1 = bc; u2 = 0; zr = zi;
-          a = an - f * bc; bc = en; zi = zn - f * zi;
-        } else {  // interchange with row i+1
-          const T f = a / ei;
-          u0 = ei; u1 = an; u2 = en; zr = zn;
-          a = bc - f * an; bc = -f * en; zi = zi - f * zn;
-        }
-        T* w = WS + (size_t)3 * i * keep + q;
-        w[0] = u0;
-        w[keep] = u1;
-        w[2 * (size_t)keep] = u2;
-        Z[(size_t)i * keep + q] = zr;
-      }
-      if (a == (T)0) a = tiny;
-      T x1 = zi / a, x2 = 0, mx = fabs(x1);
-      Z[(size_t)(p - 1) * keep + q] = x1;
-      for (int i = p - 2; i >= 0; --i) {
-        const T* w = WS + (size_t)3 * i * keep + q;
-        const T xi = (Z[(size_t)i * keep + q] - w[keep] * x1 - w[2 * (size_t)keep] * x2) / w[0];
-        Z[(size_t)i * keep + q] = xi;
-        x2 = x1;
-        x1 = xi;
-        mx = fmax(mx, fabs(xi));
-      }
-      const T inv = mx > (T)0 && isfinite(mx) ? (T)1 / mx : (T)1;
-      T s2 = 0;
-      for (int i = 0; i < p; ++i) {
-        const T v = Z[(size_t)i * keep + q] * inv;
-        s2 += v * v;
-      }
-      const T sc = s2 > (T)0 ? inv / sqrt(s2) : (T)1;
-      for (int i = 0; i < p; ++i) Z[(size_t)i * keep + q] *= sc;
-    }
-  }
+  for (int q = tid; q < keep; q += nt) inv_iter<T, T>(d, e, p, sig[q], Z + q, (size_t)keep, WS + q, (size_t)keep, q);
   __syncthreads();
 
   // ---- 7. classical Gram-Schmidt, twice, over the keep vectors

@@ -1,0 +1,337 @@
+// rr_wide.cu -- the Rayleigh-Ritz step of LOBPCG (Algorithm 3; as in
+// Algorithm 2) for one wide trial subspace spread over the whole GPU, by
+// tridiagonal reduction.  H = L^{-1} M L^{-T} comes from the cooperative
+// Cholesky factorisation and inverse (rr_large.cu) and two batched GEMM
+// launches; then
+//   k_trid_coop    Householder tridiagonalization of H in a working copy of
+//                  precision T (L2-resident); column c belongs to CTA
+//                  c mod gridDim.x; two grid barriers per step; the tail
+//                  scales (d, e) to unit Gershgorin norm
+//   k_trid_eig     top `keep` eigenvalues by S-section on the Sturm count
+//                  (FP32 search; FP64 refinement in a second launch for
+//                  T = double), the Ritz values and the positive count
+//   k_trid_shift   inverse-iteration shifts (sequential prefix)
+//   k_trid_invit   inverse iteration, one thread per eigenvector
+//   k_trid_backtr  Y = Q Z: every CTA applies all reflectors to its own
+//                  vectors (block-level reductions only)
+// and, by GEMM and cooperative-Cholesky launches, Cholesky-QR twice of Y and
+// Coef = L^{-T} Y.
+//
+// Vector scratch (`vb`, T elements): d, e, e2, tau, w (p each), lam, sig
+// (keep each), then doubles: tn, 1/tn, and 1024 per-CTA partial sums.
+#include "kernels.h"
+#include "tri_common.cuh"
+#include "gridbar.cuh"
+
+namespace sdpg {
+using namespace tri;
+
+template <typename T>
+struct WideVec {
+  T *d, *e, *e2, *tau, *w, *lam, *sig;
+  double *sc, *part;
+  __device__ WideVec(double* vb, int p, int keep) {
+    d = (T*)vb;
+    e = d + p;
+    e2 = e + p;
+    tau = e2 + p;
+    w = tau + p;
+    lam = w + p;
+    sig = lam + keep;
+    sc = vb + (((size_t)(5 * p + 2 * keep) * sizeof(T) + 7) / 8);
+    part = sc + 2;
+  }
+};
+
+__device__ __forceinline__ bool bar_failed(const GridBar* b) {
+  return *(const volatile int*)&b->fail || *(const volatile int*)&b->err;
+}
+
+// block-wide sum, result returned to every thread (two barriers)
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  T s = lane < nw ? red[lane] : (T)0;
+  return warp_sum(s);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_trid_coop(const double* H, T* A, int p, int keep, double* vb, GridBar* b) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* vs = (T*)smraw;  // Householder vector of the step (v_0 = 1)
+  T* ws = vs + p;     // w = tau A22 v of the step
+  __shared__ T red[32];
+  __shared__ T scal[4];
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  const int G = gridDim.x, bid = blockIdx.x;
+  WideVec<T> V(vb, p, keep);
+  if (bar_failed(b)) return;
+  // working copy, symmetrized: CTA bid owns the columns c = bid mod G
+  for (int c = bid; c < p; c += G)
+    for (int i = tid; i < p; i += nt) A[(size_t)c * p + i] = (T)(0.5 * (H[(size_t)c * p + i] + H[(size_t)i * p + c]));
+  if (!gbar(b)) return;
+  for (int k = 0; k + 2 < p; ++k) {
+    const int r = p - k - 1;
+    const T* colk = A + (size_t)k * p + (k + 1);
+    // Householder reflector P = I - t v v^T mapping x = A[k+1:, k] to beta e_1,
+    // computed by every CTA from the same data
+    T s = 0;
+    for (int i = 1 + tid; i < r; i += nt) {
+      const T x = __ldcg(colk + i);  // column k was updated by its owner: read past L1
+      s += x * x;
+    }
+    s = block_sum(s, red);
+    if (tid == 0) {
+      const T x0 = __ldcg(colk);
+      T beta = x0, t = 0, scale = 0;
+      if (s > (T)0) {
+        const T alpha = sqrt(x0 * x0 + s);
+        beta = x0 >= (T)0 ? -alpha : alpha;
+        t = (beta - x0) / beta;
+        scale = (T)1 / (x0 - beta);
+      }
+      scal[0] = beta;
+      scal[1] = t;
+      scal[2] = scale;
+    }
+    __syncthreads();
+    const T beta = scal[0], t = scal[1], scale = scal[2];
+    for (int i = tid; i < r; i += nt) vs[i] = i == 0 ? (T)1 : __ldcg(colk + i) * scale;
+    __syncthreads();
+    const int cfirst = k + 1 + ((bid - (k + 1)) % G + G) % G;  // first owned column of the block
+    if (t != (T)0) {
+      // w_c = t A22[:, c] . v on the owned columns (symmetric: column = row)
+      T pw = 0;
+      for (int c = cfirst + wid * G; c < p; c += nw * G) {
+        const T* col = A + (size_t)c * p + (k + 1);
+        T acc = 0;
+        for (int i = lane; i < r; i += 32) acc += col[i] * vs[i];
+        acc = warp_sum(acc) * t;
+        if (lane == 0) {
+          V.w[c] = acc;
+          pw += acc * vs[c - k - 1];
+        }
+      }
+      pw = block_sum(pw, red);
+      if (tid == 0) V.part[bid] = (double)pw;
+    }
+    if (!gbar(b)) return;  // column k read by every CTA; w and partials complete
+    if (k % G == bid) {    // the owner keeps v below the subdiagonal and (d_k, e_k, tau_k)
+      T* ck = A + (size_t)k * p + (k + 1);
+      for (int i = 1 + tid; i < r; i += nt) ck[i] = vs[i];
+      if (tid == 0) {
+        V.d[k] = A[(size_t)k * p + k];
+        V.e[k] = beta;
+        V.tau[k] = t;
+      }
+    }
+    if (t != (T)0) {
+      if (tid < 32) {  // K = t/2 w^T v over all CTAs, fixed order
+        T kk = 0;
+        for (int g = lane; g < G; g += 32) kk += (T)__ldcg(V.part + g);
+        kk = warp_sum(kk);
+        if (lane == 0) scal[3] = kk * (T)0.5 * t;
+      }
+      for (int i = tid; i < r; i += nt) ws[i] = __ldcg(V.w + k + 1 + i);
+      __syncthreads();
+      const T K = scal[3];
+      // A22[:, c] -= v w'_c + w' v_c, w' = w - K v, on the owned columns
+      for (int c = cfirst + wid * G; c < p; c += nw * G) {
+        T* col = A + (size_t)c * p + (k + 1);
+        const int jc = c - k - 1;
+        const T vc = vs[jc], wc = ws[jc] - K * vc;
+        for (int i = lane; i < r; i += 32) col[i] -= vs[i] * wc + (ws[i] - K * vs[i]) * vc;
+      }
+    }
+    if (!gbar(b)) return;
+  }
+  if (bid != 0) return;
+  // tail (CTA 0): last 2 x 2 block, Gershgorin scaling, e^2
+  if (tid == 0) {
+    if (p >= 2) {
+      V.d[p - 2] = __ldcg(A + (size_t)(p - 2) * p + (p - 2));
+      V.d[p - 1] = __ldcg(A + (size_t)(p - 1) * p + (p - 1));
+      V.e[p - 2] = __ldcg(A + (size_t)(p - 2) * p + (p - 1));
+    } else {
+      V.d[0] = __ldcg(A);
+    }
+  }
+  __syncthreads();
+  // (d, e) were written by the owners of their columns: read past L1
+  T lo = 0, hi = 0;
+  int bad = 0;
+  for (int i = tid; i < p; i += nt) {
+    const T di = __ldcg(V.d + i);
+    const T off = (i > 0 ? fabs(__ldcg(V.e + i - 1)) : (T)0) + (i + 1 < p ? fabs(__ldcg(V.e + i)) : (T)0);
+    lo = fmin(lo, di - off);
+    hi = fmax(hi, di + off);
+    bad |= !isfinite(di) || !isfinite(off);
+  }
+  lo = warp_min(lo);
+  hi = warp_max(hi);
+  bad = __syncthreads_or(bad);
+  __shared__ T rlo[32], rhi[32];
+  if (lane == 0) {
+    rlo[wid] = lo;
+    rhi[wid] = hi;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    T l = 0, h = 0;
+    for (int w2 = 0; w2 < nw; ++w2) {
+      l = fmin(l, rlo[w2]);
+      h = fmax(h, rhi[w2]);
+    }
+    T nrm = fmax(fabs(l), fabs(h));
+    nrm = nrm > (T)0 ? nrm : (T)1;
+    V.sc[0] = (double)nrm;
+    V.sc[1] = 1.0 / (double)nrm;
+    scal[0] = (T)1 / nrm;
+    if (bad) atomicCAS(&b->fail, 0, -3);  // non-finite data: breakdown
+  }
+  __syncthreads();
+  const T itn = scal[0];
+  for (int i = tid; i < p; i += nt) {
+    V.d[i] = __ldcg(V.d + i) * itn;
+    if (i + 1 < p) {
+      const T ei = __ldcg(V.e + i) * itn;
+      V.e[i] = ei;
+      V.e2[i] = ei * ei;
+    }
+  }
+}
+
+// Top `keep` eigenvalues of the scaled tridiagonal.  TS is the precision of
+// the search: float for the wide search, T = double for the refinement
+// (refine = 1, from the FP32 bracket).  The last launch of a step
+// (final = 1) writes the Ritz values theta = tn lam and the positive count.
+template <typename TS, typename T>
+__global__ void __launch_bounds__(256) k_trid_eig(double* vb, int p, int keep, int S, int refine, int final,
+                                                  double* theta, int* npos, const GridBar* b) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  TS* ds = (TS*)smraw;
+  TS* e2s = ds + p;
+  WideVec<T> V(vb, p, keep);
+  if (bar_failed(b)) return;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < p; i += nt) {
+    ds[i] = (TS)V.d[i];
+    e2s[i] = i + 1 < p ? (TS)V.e2[i] : (TS)0;
+  }
+  __syncthreads();
+  const int gpb = nt / S;
+  const TS tol = refine ? (TS)4 * K<TS>::eps : (sizeof(T) == sizeof(float) ? 4 : 32) * (TS)K<float>::eps;
+  if (refine)
+    section_search<TS, T>(ds, e2s, p, keep, S, blockIdx.x * gpb + tid / S, gridDim.x * gpb, tol,
+                          (TS)(64.0f * K<float>::eps), (TS)0, K<TS>::safmin, V.lam, true);
+  else
+    section_search<TS, T>(ds, e2s, p, keep, S, blockIdx.x * gpb + tid / S, gridDim.x * gpb, tol, (TS)-1.01,
+                          (TS)1.01, K<TS>::safmin, V.lam, false);
+  if (!final) return;
+  __syncthreads();
+  // the lanes that wrote lam[q] publish theta[q] (same group mapping)
+  const int g = blockIdx.x * gpb + tid / S;
+  if (tid % S == 0)
+    for (int q = g; q < keep; q += gridDim.x * gpb) theta[q] = (double)V.lam[q] * V.sc[0];
+  if (blockIdx.x == 0 && tid == 0) {
+    const T* d = V.d;
+    const T* e2 = V.e2;
+    *npos = p - sturm_below(d, e2, p, (T)0, (T)K<T>::safmin);
+  }
+}
+
+// Inverse-iteration shifts: at least 10 eps apart, so that equal
+// eigenvalues get distinct vectors.
+template <typename T>
+__global__ void k_trid_shift(double* vb, int p, int keep, const GridBar* b) {
+  WideVec<T> V(vb, p, keep);
+  if (bar_failed(b) || threadIdx.x != 0 || blockIdx.x != 0) return;
+  const T sep = (T)10 * K<T>::eps;
+  T prev = V.lam[0];
+  V.sig[0] = prev;
+  for (int q = 1; q < keep; ++q) {
+    T s = V.lam[q];
+    if (s < prev + sep) s = prev + sep;
+    V.sig[q] = s;
+    prev = s;
+  }
+}
+
+// One thread per eigenvector: Z[:, q] (column-major, ld p, FP64 storage).
+template <typename T>
+__global__ void __launch_bounds__(128) k_trid_invit(double* vb, int p, int keep, double* Z, T* WS, const GridBar* b) {
+  WideVec<T> V(vb, p, keep);
+  if (bar_failed(b)) return;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= keep) return;
+  inv_iter<T, double>(V.d, V.e, p, V.sig[q], Z + (size_t)q * p, 1, WS + q, (size_t)keep, q);
+}
+
+// Y = Q Z = P_0 P_1 ... P_{p-3} Z for the vectors [q0, q0 + nv) of this CTA
+// (nv <= kTridBacktrNv); thread t owns the rows t, t + nt, ... of every one of
+// them, so no barrier separates the update by one reflector from the dot
+// products of the next.
+template <typename T>
+__global__ void __launch_bounds__(256) k_trid_backtr(const T* A, double* vb, int p, int keep, double* Y, int nv,
+                                                     const GridBar* b) {
+  __shared__ T red[8][kTridBacktrNv];
+  __shared__ T sj[kTridBacktrNv];
+  WideVec<T> V(vb, p, keep);
+  if (bar_failed(b)) return;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  const int q0 = blockIdx.x * nv, nq = min(nv, keep - q0);
+  if (nq <= 0) return;
+  double* Yb = Y + (size_t)q0 * p;
+  for (int k = p - 3; k >= 0; --k) {
+    const T t = V.tau[k];
+    if (t == (T)0) continue;
+    const T* vk = A + (size_t)k * p;  // v_k[i] for i >= k + 2; v_k[k + 1] = 1
+    const int i0 = tid >= k + 1 ? tid : tid + ((k + 1 - tid + nt - 1) / nt) * nt;
+    T acc[kTridBacktrNv];
+#pragma unroll
+    for (int j = 0; j < kTridBacktrNv; ++j) acc[j] = 0;
+    for (int i = i0; i < p; i += nt) {
+      const T vi = i == k + 1 ? (T)1 : vk[i];
+#pragma unroll
+      for (int j = 0; j < kTridBacktrNv; ++j)
+        if (j < nq) acc[j] += vi * (T)Yb[(size_t)j * p + i];
+    }
+#pragma unroll
+    for (int j = 0; j < kTridBacktrNv; ++j) {
+      if (j >= nq) break;
+      const T s = warp_sum(acc[j]);
+      if (lane == 0) red[wid][j] = s;
+    }
+    __syncthreads();
+    if (tid < nq) {
+      T s = 0;
+      for (int w2 = 0; w2 < nw; ++w2) s += red[w2][tid];
+      sj[tid] = t * s;
+    }
+    __syncthreads();
+    for (int i = i0; i < p; i += nt) {
+      const T vi = i == k + 1 ? (T)1 : vk[i];
+#pragma unroll
+      for (int j = 0; j < kTridBacktrNv; ++j)
+        if (j < nq) Yb[(size_t)j * p + i] = (double)((T)Yb[(size_t)j * p + i] - vi * sj[j]);
+    }
+  }
+}
+
+template __global__ void k_trid_coop<float>(const double*, float*, int, int, double*, GridBar*);
+template __global__ void k_trid_coop<double>(const double*, double*, int, int, double*, GridBar*);
+template __global__ void k_trid_eig<float, float>(double*, int, int, int, int, int, double*, int*, const GridBar*);
+template __global__ void k_trid_eig<float, double>(double*, int, int, int, int, int, double*, int*, const GridBar*);
+template __global__ void k_trid_eig<double, double>(double*, int, int, int, int, int, double*, int*, const GridBar*);
+template __global__ void k_trid_shift<float>(double*, int, int, const GridBar*);
+template __global__ void k_trid_shift<double>(double*, int, int, const GridBar*);
+template __global__ void k_trid_invit<float>(double*, int, int, double*, float*, const GridBar*);
+template __global__ void k_trid_invit<double>(double*, int, int, double*, double*, const GridBar*);
+template __global__ void k_trid_backtr<float>(const float*, double*, int, int, double*, int, const GridBar*);
+template __global__ void k_trid_backtr<double>(const double*, double*, int, int, double*, int, const GridBar*);
+
+}  // namespace sdpg

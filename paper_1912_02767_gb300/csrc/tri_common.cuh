@@ -1,0 +1,171 @@
+// tri_common.cuh -- device helpers shared by the Rayleigh-Ritz eigensolvers
+// that work on a symmetric tridiagonal matrix (rr_tri.cu: one CTA per
+// instance; rr_wide.cu: a wide subspace across the GPU): Sturm counts,
+// S-section search for selected eigenvalues (bisection on the Sturm count),
+// and inverse iteration by Gaussian elimination with partial pivoting.
+#pragma once
+#include "common.cuh"
+
+namespace sdpg {
+namespace tri {
+
+template <typename T>
+struct K;
+template <>
+struct K<float> {
+  static constexpr float piv_min = 1e-6f;           // Cholesky-QR breakdown (Gram of unit columns)
+  static constexpr float eps = 5.9604645e-08f;      // unit roundoff 2^-24
+  static constexpr float safmin = 1.17549435e-38f;  // smallest normal
+};
+template <>
+struct K<double> {
+  static constexpr double piv_min = 1e-12;
+  static constexpr double eps = 1.1102230246251565e-16;  // 2^-53
+  static constexpr double safmin = 2.2250738585072014e-308;
+};
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_min(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Number of eigenvalues of the symmetric tridiagonal (d, e) below x: the
+// count of negative pivots of the LDL^T factorization of T - x I (Sturm
+// sequence).  A pivot smaller than pivmin in magnitude is replaced by
+// -pivmin, which keeps the count monotone in x.
+template <typename T>
+__device__ __forceinline__ int sturm_below(const T* d, const T* e2, int p, T x, T pivmin) {
+  T q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  int c = q < (T)0;
+  for (int i = 1; i < p; ++i) {
+    q = (d[i] - x) - e2[i - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    c += q < (T)0;
+  }
+  return c;
+}
+
+// Start vector of inverse iteration: uniform in [-1, 1) from the Philox
+// stream keyed for this purpose (row i, vector q).
+template <typename T>
+__device__ __forceinline__ T start_value(int i, int q) {
+  uint32_t c[4] = {(uint32_t)i, (uint32_t)q, 0x52525452u, 0u};
+  philox4x32_10(c, 0x7452694Eu, 0x49544552u);
+  return (T)((double)c[0] * (1.0 / 2147483648.0) - 1.0);
+}
+
+// S-section search for eigenvalues p-keep .. p-1 (ascending) of the
+// tridiagonal (d, e2 = e^2) whose spectrum lies in [-1.01, 1.01]: lane
+// groups of S (a power of two <= 32) per eigenvalue, each lane counting at
+// one of S interior points per step, until the bracket is narrower than tol.
+// Group g of `ngroups` (numbered across the whole launch by the caller)
+// handles q = g, g + ngroups, ...  refine = false: start from [lo0, hi0];
+// refine = true: start from lam[q] -/+ lo0 (checked by two counts, else the
+// whole [-1.01, 1.01]).  Writes lam[q] (midpoint) from the group's lane 0.
+template <typename TS, typename TL>
+__device__ void section_search(const TS* d, const TS* e2, int p, int keep, int S, int g, int ngroups, TS tol, TS lo0,
+                               TS hi0, TS pivmin, TL* lam, bool refine) {
+  const int lane = threadIdx.x & 31, sl = threadIdx.x % S;
+  const unsigned gbase = (unsigned)(lane & ~(S - 1));
+  const unsigned gmask = S == 32 ? 0xffffffffu : (((1u << S) - 1u) << gbase);
+  for (int q = g; q < keep; q += ngroups) {  // lanes of a group share q: group-uniform
+    const int J = p - keep + q;
+    TS lo = lo0, hi = hi0;
+    if (refine) {
+      const TS c = (TS)lam[q];
+      lo = c - lo0;
+      hi = c + lo0;
+      const int clo = sturm_below(d, e2, p, lo, pivmin), chi = sturm_below(d, e2, p, hi, pivmin);
+      if (!(clo <= J && J < chi)) {
+        lo = (TS)-1.01;
+        hi = (TS)1.01;
+      }
+    }
+    for (int it = 0; it < 200 && hi - lo > tol; ++it) {
+      const TS step = (hi - lo) / (TS)(S + 1);
+      const int c = sturm_below(d, e2, p, lo + step * (TS)(sl + 1), pivmin);
+      unsigned b = __ballot_sync(gmask, c > J) >> gbase;
+      if (S < 32) b &= (1u << S) - 1u;
+      const int f = __ffs(b) - 1;  // first point above eigenvalue J (-1: none)
+      const TS nlo = f < 0 ? lo + step * (TS)S : (f == 0 ? lo : lo + step * (TS)f);
+      const TS nhi = f < 0 ? hi : lo + step * (TS)(f + 1);
+      if (nlo == lo && nhi == hi) break;  // no representable progress
+      lo = nlo;
+      hi = nhi;
+    }
+    if (sl == 0) lam[q] = (TL)((TS)0.5 * (lo + hi));
+  }
+}
+
+// Inverse iteration for the eigenvector of the tridiagonal (d, e) nearest
+// the shift sg: three solves of (T - sg I) x = z by Gaussian elimination
+// with partial pivoting (U has two superdiagonals, a zero pivot becomes
+// tiny), from the Philox start vector of column q, normalized each time.
+// The vector lives at z[i * zs] (element type TZ), the factors at
+// w[(3 i + c) * ws], c = 0, 1, 2.
+template <typename T, typename TZ>
+__device__ void inv_iter(const T* __restrict__ d, const T* __restrict__ e, int p, T sg, TZ* __restrict__ z, size_t zs,
+                         T* __restrict__ w, size_t ws, int q) {
+  const T tiny = K<T>::eps;
+  for (int i = 0; i < p; ++i) z[(size_t)i * zs] = (TZ)start_value<T>(i, q);
+  for (int it = 0; it < 3; ++it) {
+    T a = d[0] - sg, bc = p > 1 ? e[0] : (T)0, zi = (T)z[0];
+    for (int i = 0; i + 1 < p; ++i) {
+      const T ei = e[i], an = d[i + 1] - sg, en = i + 2 < p ? e[i + 1] : (T)0;
+      const T zn = (T)z[(size_t)(i + 1) * zs];
+      T u0, u1, u2, zr;
+      if (fabs(a) >= fabs(ei)) {  // pivot on the active row
+        if (a == (T)0) a = tiny;
+        const T f = ei / a;
+        u0 = a; u1 = bc; u2 = 0; zr = zi;
+        a = an - f * bc; bc = en; zi = zn - f * zi;
+      } else {  // interchange with row i+1
+        const T f = a / ei;
+        u0 = ei; u1 = an; u2 = en; zr = zn;
+        a = bc - f * an; bc = -f * en; zi = zi - f * zn;
+      }
+      T* wi = w + (size_t)3 * i * ws;
+      wi[0] = u0;
+      wi[ws] = u1;
+      wi[2 * ws] = u2;
+      z[(size_t)i * zs] = (TZ)zr;
+    }
+    if (a == (T)0) a = tiny;
+    T x1 = zi / a, x2 = 0, mx = fabs(x1);
+    z[(size_t)(p - 1) * zs] = (TZ)x1;
+    for (int i = p - 2; i >= 0; --i) {
+      const T* wi = w + (size_t)3 * i * ws;
+      const T xi = ((T)z[(size_t)i * zs] - wi[ws] * x1 - wi[2 * ws] * x2) / wi[0];
+      z[(size_t)i * zs] = (TZ)xi;
+      x2 = x1;
+      x1 = xi;
+      mx = fmax(mx, fabs(xi));
+    }
+    const T inv = mx > (T)0 && isfinite(mx) ? (T)1 / mx : (T)1;
+    T s2 = 0;
+    for (int i = 0; i < p; ++i) {
+      const T v = (T)z[(size_t)i * zs] * inv;
+      s2 += v * v;
+    }
+    const T sc = s2 > (T)0 ? inv / sqrt(s2) : (T)1;
+    for (int i = 0; i < p; ++i) z[(size_t)i * zs] = (TZ)((T)z[(size_t)i * zs] * sc);
+  }
+}
+
+}  // namespace tri
+}  // namespace sdpg
