@@ -98,6 +98,9 @@ __global__ void k_trid_invit(double* vb, int p, int keep, double* Z, T* WS, cons
 template <typename T>
 __global__ void k_trid_backtr(const T* A, double* vb, int p, int keep, double* Y, int nv, const GridBar* b);
 constexpr int kTridBacktrNv = 16;  // vectors per CTA of k_trid_backtr (at most)
+// dynamic shared memory of k_trid_backtr: nv vectors, three reflector buffers, tau
+inline size_t rr_backtr_smem_bytes(int p, int nv, int tsize) { return (size_t)(nv + 4) * p * tsize; }
+constexpr size_t kBacktrSmemMax = 230400;  // 227 KiB per CTA less the kernel's static shared memory (<= 2 KiB)
 
 // jacobi_kernels.cu (exact branch)
 __global__ void k_jac_init(Inst* insts, WorkMap wm, int negate);

@@ -272,12 +272,16 @@ __global__ void __launch_bounds__(128) k_trid_invit(double* vb, int p, int keep,
 }
 
 // Y = Q Z = P_0 P_1 ... P_{p-3} Z for the vectors [q0, q0 + nv) of this CTA
-// (nv <= kTridBacktrNv); thread t owns the rows t, t + nt, ... of every one of
-// them, so no barrier separates the update by one reflector from the dot
-// products of the next.
+// (nv <= kTridBacktrNv), held in shared memory for the whole product; the
+// reflectors stream through a triple buffer (v_{k-1} is fetched while v_k is
+// applied, and is never written while a slower thread still reads v_{k+1}).
+// Thread t owns the rows t, t + nt, ... of every vector, so no barrier
+// separates the update by one reflector from the dot products of the next.
+// Dynamic shared memory: rr_backtr_smem_bytes(p, nv, sizeof(T)).
 template <typename T>
 __global__ void __launch_bounds__(256) k_trid_backtr(const T* A, double* vb, int p, int keep, double* Y, int nv,
                                                      const GridBar* b) {
+  extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ T red[8][kTridBacktrNv];
   __shared__ T sj[kTridBacktrNv];
   WideVec<T> V(vb, p, keep);
@@ -285,20 +289,39 @@ __global__ void __launch_bounds__(256) k_trid_backtr(const T* A, double* vb, int
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   const int q0 = blockIdx.x * nv, nq = min(nv, keep - q0);
   if (nq <= 0) return;
+  T* Ys = (T*)smraw;                // nq x p
+  T* vbuf = Ys + (size_t)nv * p;    // 3 x p
+  T* taus = vbuf + (size_t)3 * p;   // p
   double* Yb = Y + (size_t)q0 * p;
+  for (int j = 0; j < nq; ++j)
+    for (int i = tid; i < p; i += nt) Ys[(size_t)j * p + i] = (T)Yb[(size_t)j * p + i];
+  for (int i = tid; i < p; i += nt) taus[i] = i + 2 < p ? V.tau[i] : (T)0;
+  if (p >= 3) {
+    const int k = p - 3;
+    T* vn = vbuf + (size_t)(k % 3) * p;
+    for (int i = k + 1 + tid; i < p; i += nt) vn[i] = i == k + 1 ? (T)1 : A[(size_t)k * p + i];
+  }
+  __syncthreads();
   for (int k = p - 3; k >= 0; --k) {
-    const T t = V.tau[k];
-    if (t == (T)0) continue;
-    const T* vk = A + (size_t)k * p;  // v_k[i] for i >= k + 2; v_k[k + 1] = 1
+    if (k > 0) {  // fetch v_{k-1} (rows >= k) into the next buffer
+      T* vn = vbuf + (size_t)((k - 1) % 3) * p;
+      for (int i = k + tid; i < p; i += nt) vn[i] = i == k ? (T)1 : A[(size_t)(k - 1) * p + i];
+    }
+    const T t = taus[k];
+    if (t == (T)0) {
+      __syncthreads();  // keeps the buffer rotation in step
+      continue;
+    }
+    const T* vs = vbuf + (size_t)(k % 3) * p;
     const int i0 = tid >= k + 1 ? tid : tid + ((k + 1 - tid + nt - 1) / nt) * nt;
     T acc[kTridBacktrNv];
 #pragma unroll
     for (int j = 0; j < kTridBacktrNv; ++j) acc[j] = 0;
     for (int i = i0; i < p; i += nt) {
-      const T vi = i == k + 1 ? (T)1 : vk[i];
+      const T vi = vs[i];
 #pragma unroll
       for (int j = 0; j < kTridBacktrNv; ++j)
-        if (j < nq) acc[j] += vi * (T)Yb[(size_t)j * p + i];
+        if (j < nq) acc[j] += vi * Ys[(size_t)j * p + i];
     }
 #pragma unroll
     for (int j = 0; j < kTridBacktrNv; ++j) {
@@ -314,12 +337,15 @@ __global__ void __launch_bounds__(256) k_trid_backtr(const T* A, double* vb, int
     }
     __syncthreads();
     for (int i = i0; i < p; i += nt) {
-      const T vi = i == k + 1 ? (T)1 : vk[i];
+      const T vi = vs[i];
 #pragma unroll
       for (int j = 0; j < kTridBacktrNv; ++j)
-        if (j < nq) Yb[(size_t)j * p + i] = (double)((T)Yb[(size_t)j * p + i] - vi * sj[j]);
+        if (j < nq) Ys[(size_t)j * p + i] -= vi * sj[j];
     }
   }
+  __syncthreads();
+  for (int j = 0; j < nq; ++j)
+    for (int i = tid; i < p; i += nt) Yb[(size_t)j * p + i] = (double)Ys[(size_t)j * p + i];
 }
 
 template __global__ void k_trid_coop<float>(const double*, float*, int, int, double*, GridBar*);
