@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--count", type=int, default=64, help="instances (batch) or requests (serve)")
     ap.add_argument("--rr", type=int, default=0, choices=[0, 1],
                     help="Rayleigh-Ritz eigensolver: 0 tridiagonal where it fits (default), 1 Jacobi")
+    ap.add_argument("--rr-prec", default="fp32", choices=["fp32", "fp64"],
+                    help="projection sweep, mixed path: Rayleigh-Ritz precision (the sweep's spectra have a gap "
+                         "at zero, |lambda| >= 0.1, so FP32 keeps the closed-form error at the mixed level)")
     ap.add_argument("--kernel", default=None, choices=[None, "product"],
                     help="time one kernel alone: 'product' = W B on the tensor cores (sdp_block_product)")
     ap.add_argument("--n", type=int, default=6144)
@@ -395,7 +398,8 @@ def main():
     sdpgpu.load()
     prec = sdpgpu.PREC_FP64 if args.prec == "fp64" else sdpgpu.PREC_BF16X3
     stream = torch.cuda.current_stream()
-    ctx = sdpgpu.Context(stream=stream, precision=prec, rr_method=args.rr)
+    ctx = sdpgpu.Context(stream=stream, precision=prec, rr_method=args.rr,
+                         rr_fp32=1 if (args.prec != "fp64" and args.rr_prec == "fp32") else 0)
     mats = make_mats(args)
     dev = []
     for m in mats:
@@ -553,7 +557,9 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": "psd_projection_sweep",
                            "matrices": ["n=%d k/n=%g" % (m["n"], m["f"]) for m in mats],
-                           "precision": args.prec, "l2": "flushed between steps (256 MiB write)",
+                           "precision": args.prec,
+                           "rayleigh_ritz": "fp64" if (args.prec == "fp64" or args.rr_prec == "fp64") else "fp32",
+                           "l2": "flushed between steps (256 MiB write)",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "fp64_path": fp64_path,

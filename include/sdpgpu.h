@@ -83,7 +83,10 @@ typedef struct {
   int rr_method;       /* Rayleigh-Ritz eigensolver: 0 tridiagonal reduction where the   */
                        /* p x p matrix fits one CTA's shared memory, Jacobi above;        */
                        /* 1 Jacobi at every width (comparator)            default 0     */
-  int reserved;        /* must be 0                                                     */
+  int rr_fp32;         /* 1: with BF16X3, Rayleigh-Ritz (Cholesky-QR + eigensolver) in     */
+                       /* FP32 instead of FP64 -- only for spectra whose kept eigenvalues  */
+                       /* are not small against ||W|| (e.g. a standalone projection with a */
+                       /* gap at zero); ADMM near a rank change needs FP64   default 0     */
 } sdp_settings;
 
 typedef struct {

@@ -93,7 +93,7 @@ extern "C" void sdp_default_settings(sdp_settings* s) {
   s->mode_frac = 1.0 / 3.0;
   s->seed = 0;
   s->rr_method = 0;
-  s->reserved = 0;
+  s->rr_fp32 = 0;
 }
 
 extern "C" const char* sdp_status_str(int s) {
@@ -118,7 +118,7 @@ extern "C" const char* sdp_status_str(int s) {
 static bool settings_ok(const sdp_settings* s) {
   return s->rho > 0 && s->sigma > 0 && s->alpha > 0 && s->alpha < 2 && s->eps_abs >= 0 && s->eps_rel >= 0 &&
          s->max_iter >= 1 && s->check_every >= 1 && s->lobpcg_max_iter >= 1 && s->precision >= 0 &&
-         s->precision <= 2 && (s->rr_method == 0 || s->rr_method == 1) && s->reserved == 0 && s->tol_coef > 0 && s->expand_frac > 0 && s->mode_frac > 0 && s->mode_frac <= 0.5;
+         s->precision <= 2 && (s->rr_method == 0 || s->rr_method == 1) && (s->rr_fp32 == 0 || s->rr_fp32 == 1) && s->tol_coef > 0 && s->expand_frac > 0 && s->mode_frac > 0 && s->mode_frac <= 0.5;
 }
 
 // ---------------------------------------------------------------------------

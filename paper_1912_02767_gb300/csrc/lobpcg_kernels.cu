@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(1024) k_rayleigh_ritz(Inst* insts, const int* 
   for (int j = 0; j < p; ++j) {
     if (threadIdx.x == 0) {
       T d = (T)G[idx2(j, j, p)];
-      if (!(d > (T)RRConst<T>::piv_min)) fail = j + 1;
+      if (!(d > (T)(I.prec != 0 ? 1e-6 : RRConst<T>::piv_min))) fail = j + 1;
       else G[idx2(j, j, p)] = (double)sqrt(d);
     }
     __syncthreads();
@@ -615,7 +615,7 @@ __global__ void __launch_bounds__(1024) k_rr_smem(Inst* insts, const int* list, 
   for (int j = 0; j < p; ++j) {
     if (tid == 0) {
       T d = A[j + j * p];
-      if (!(d > (T)RRConst<T>::piv_min)) fail = j + 1;
+      if (!(d > (T)(I.prec != 0 ? 1e-6 : RRConst<T>::piv_min))) fail = j + 1;
       A[j + j * p] = sqrt(d > (T)0 ? d : (T)1);
     }
     __syncthreads();

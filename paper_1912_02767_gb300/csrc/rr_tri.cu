@@ -63,6 +63,9 @@ __global__ void __launch_bounds__(1024) k_rr_tri(Inst* insts, const int* list, i
   __shared__ T s_red[32];
   __shared__ T s_sc[2];
 
+  // breakdown threshold of Cholesky-QR: set by the precision the Gram was
+  // formed in (FP32 Grams in the mixed modes), not by this kernel's type
+  const T piv = I.prec != 0 ? (T)1e-6 : (T)1e-12;
   // ---- 1. G = L~ D L~^T (right-looking, lower triangle of B)
   for (int t = tid; t < p * p; t += nt) {
     const int i = t % p, j = t / p;
@@ -72,7 +75,7 @@ __global__ void __launch_bounds__(1024) k_rr_tri(Inst* insts, const int* list, i
   __syncthreads();
   for (int j = 0; j < p; ++j) {
     const T djj = B[j + j * ldp];
-    if (!(djj > (T)K<T>::piv_min)) {
+    if (!(djj > piv)) {
       if (tid == 0) s_fail = j + 1;
       break;  // every thread reads the same pivot: uniform exit
     }
