@@ -57,9 +57,10 @@ typedef enum {
  * infeasibility tests are FP64 in every mode. */
 typedef enum {
   SDP_PREC_FP64 = 0,    /* every product, Gram and Rayleigh-Ritz in FP64 (CUDA cores)          */
-  SDP_PREC_BF16X3 = 1,  /* W*S and reconstruction on tcgen05 tensor cores with split-BF16 x3, FP32 */
-                        /* accumulate; Grams/Rayleigh-Ritz/Cholesky-QR in FP32, residual norms FP64 */
-  SDP_PREC_AUTO = 2     /* BF16X3 while the LOBPCG tolerance is above its error floor, else FP64 */
+  SDP_PREC_BF16X3 = 1,  /* W*S on tcgen05 tensor cores with split-BF16 x3, FP32 accumulate; Grams,  */
+                        /* block update and reconstruction in FP32; Rayleigh-Ritz in FP64 (FP32 by   */
+                        /* the rr_fp32 setting); residual norms, ADMM state and tests FP64            */
+  SDP_PREC_AUTO = 2     /* accepted; computes as SDP_PREC_BF16X3 (no tolerance-driven switch yet) */
 } sdp_precision;
 
 typedef struct {
@@ -80,9 +81,10 @@ typedef struct {
   double expand_frac;  /* expansion block b = ceil(expand_frac*n) (Section 4) default 1/50 */
   double mode_frac;    /* positive/negative mode threshold (Section 5)     default 1/3   */
   unsigned long long seed; /* Philox key for the random expansion columns  default 0     */
-  int rr_method;       /* Rayleigh-Ritz eigensolver: 0 tridiagonal reduction where the   */
-                       /* p x p matrix fits one CTA's shared memory, Jacobi above;        */
-                       /* 1 Jacobi at every width (comparator)            default 0     */
+  int rr_method;       /* Rayleigh-Ritz eigensolver: 0 tridiagonal reduction (Householder,*/
+                       /* Sturm bisection, inverse iteration) on one CTA while the p x p  */
+                       /* matrix fits its shared memory, across the GPU above; 1 cyclic    */
+                       /* Jacobi at every width (comparator)              default 0     */
   int rr_fp32;         /* 1: with BF16X3, Rayleigh-Ritz (Cholesky-QR + eigensolver) in     */
                        /* FP32 instead of FP64 -- only for spectra whose kept eigenvalues  */
                        /* are not small against ||W|| (e.g. a standalone projection with a */
@@ -186,7 +188,9 @@ int sdp_block_product(sdp_ctx* ctx, int n, const double* W, const double* B, int
 
 /* Solve `count` set-up contexts together: every ADMM step of all of them is
  * issued as one batched launch sequence (one launch per kernel for the
- * whole group), captured once in a CUDA graph and replayed.  All contexts
+ * whole group, each CTA finding its instance through a prefix map); the
+ * LOBPCG loop is host-driven (its step count and subspace widths are read
+ * back per step), so the sequence is not a CUDA graph.  All contexts
  * must share precision, rho, sigma, alpha, check_every and max_iter.
  * info (count entries) may be NULL.  Returns SDP_OK when every instance
  * finished (each info[k].status holds its own result). */
