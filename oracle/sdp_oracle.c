@@ -41,7 +41,7 @@
  *
  * Readings of the paper (where it is silent or garbled) are fixed here and
  * repeated in the design notes:
- *   - Algorithm 1 line 4 is read as y <- y + rho(alpha z~ + (1-alpha) z - z+),
+ *   - the dual update of Algorithm 1 is read as y <- y + rho(alpha z~ + (1-alpha) z - z+),
  *     so Y+ = rho (W - Pi(W)) and y_e+ = rho (w_e - b).
  *   - Eq. at the end of Section 4 "Pi = I - V- Lambda- V-^T" is read as
  *     A - V- Lambda- V-^T (Eq. 2).
@@ -601,7 +601,7 @@ int orc_lobpcg(int n, const double* A, int* m_io, int mcap, double* X, double* l
   int nfresh = 0;     /* trailing Gaussian columns not yet Ritz vectors */
   int status = ORC_OK;
   info[0] = info[1] = info[2] = info[3] = 0;
-  /* line 1: Rayleigh-Ritz on span(X^0) */
+  /* initial Rayleigh-Ritz on span(X^0) (Algorithm 3) */
   if (orc_rayleigh_ritz(n, A, m, X, RV, RL)) { status = ORC_E_NUMERICAL; goto done; }
   memcpy(X, RV, sizeof(double) * (size_t)n * m);
   memcpy(lam, RL, sizeof(double) * m);
@@ -625,7 +625,7 @@ int orc_lobpcg(int n, const double* A, int* m_io, int mcap, double* X, double* l
     info[3] = npos;
     if (allconv) { info[2] = 1; break; }
     if (it >= maxit) break;
-    /* line 6: Rayleigh-Ritz on span(X, R, Delta X), keep the m largest */
+    /* Rayleigh-Ritz on span(X, R, Delta X), keep the m largest (Algorithm 3) */
     int use_dx = (mdx > 0);
     int rc = 1;
     int p = 0;
@@ -677,7 +677,7 @@ int orc_lobpcg(int n, const double* A, int* m_io, int mcap, double* X, double* l
     }
     nfresh = 0;
     m = mkeep;
-    /* line 8: expansion */
+    /* expansion of the block (Algorithm 3) */
     if (npos_rr > m) {
       int b = bexp;
       if (m + b > mcap || m + b > n) { status = ORC_E_NOMEM; break; }
@@ -778,7 +778,7 @@ int orc_admm_solve(int n, const double* C, const orc_cons* A, const double* b, c
       memcpy(Yprev, Y, sizeof(double) * nn);
       memcpy(yeprev, ye, sizeof(double) * m);
     }
-    /* line 2: linear step.  r = sigma x - q + rho A-bar^T (z - y/rho) */
+    /* linear step (Algorithm 1).  r = sigma x - q + rho A-bar^T (z - y/rho) */
     for (int p = 0; p < m; ++p) t[p] = ze[p] - ye[p] / rho;
     for (size_t q = 0; q < nn; ++q) r[q] = sigma * x[q] - C[q] + rho * (Z[q] - Y[q] / rho);
     orc_AT_add(A, t, rho, r);
@@ -788,9 +788,9 @@ int orc_admm_solve(int n, const double* C, const orc_cons* A, const double* b, c
     orc_AT_add(A, v, -rho, xt);
     for (size_t q = 0; q < nn; ++q) xt[q] /= s;
     orc_A(A, xt, zt); /* z~ = A-bar x~ : equality block A(x~), cone block x~ */
-    /* line 3: x <- alpha x~ + (1-alpha) x */
+    /* relaxed primal update (Algorithm 1): x <- alpha x~ + (1-alpha) x */
     for (size_t q = 0; q < nn; ++q) x[q] = alpha * xt[q] + (1.0 - alpha) * x[q];
-    /* line 4: z <- Pi_C(alpha z~ + (1-alpha) z + y/rho) */
+    /* projection step (Algorithm 1): z <- Pi_C(alpha z~ + (1-alpha) z + y/rho) */
     for (int p = 0; p < m; ++p) we[p] = alpha * zt[p] + (1.0 - alpha) * ze[p] + ye[p] / rho;
     for (size_t q = 0; q < nn; ++q) W[q] = alpha * xt[q] + (1.0 - alpha) * Z[q] + Y[q] / rho;
     /* projection onto S+ */
@@ -862,7 +862,7 @@ int orc_admm_solve(int n, const double* C, const orc_cons* A, const double* b, c
       }
     }
     for (int p = 0; p < m; ++p) ze[p] = b[p];
-    /* line 5: y <- y + rho (alpha z~ + (1-alpha) z - z+) */
+    /* dual update (Algorithm 1): y <- y + rho (alpha z~ + (1-alpha) z - z+) */
     for (int p = 0; p < m; ++p) ye[p] = rho * (we[p] - b[p]);
     for (size_t q = 0; q < nn; ++q) Y[q] = rho * (W[q] - Z[q]);
     if (!check) continue;

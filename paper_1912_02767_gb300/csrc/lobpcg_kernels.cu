@@ -469,7 +469,7 @@ __global__ void k_compact(Inst* insts, WorkMap wm) {
   }
 }
 
-// Fresh Gaussian columns of the expansion (Algorithm 3, last line), from
+// Fresh Gaussian columns of the expansion (the expansion step of Algorithm 3), from
 // the same Philox stream as the oracle: (row, col, draw, stream) with
 // draw = expansion count and stream = ADMM iteration.
 __global__ void k_fill_random(Inst* insts, WorkMap wm, const int* col0, const int* ncols, const int* draw,

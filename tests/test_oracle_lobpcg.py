@@ -45,7 +45,7 @@ def test_lobpcg_converges_to_exact_projection(orc, n, f):
 
 def test_lobpcg_expansion_finds_missing_eigenpairs(orc):
     """A block that starts with fewer columns than positive eigenvalues must
-    expand with random columns (Algorithm 3, last line) and still end exact."""
+    expand with random columns (the expansion step of Algorithm 3) and still end exact."""
     rng = np.random.default_rng(3)
     n, k = 80, 12
     sp = gen.random_spectrum(n, k / n, rng)
