@@ -115,6 +115,22 @@ def run_product(args):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(dist, ms, device):
+    """The step time of the job: the maximum of the ranks' timed totals (the
+    slowest replica decides); `dist` is None for one process."""
+    if dist is None:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, max_ms):
+    """Units all ranks processed per second of the slowest rank's time."""
+    return units_per_rank * world / (max_ms / 1000.0)
+
+
 def sweep(args):
     ns = [int(x) for x in args.sizes.split(",") if x]
     fs = [float(x) for x in args.fracs.split(",") if x]
@@ -212,7 +228,12 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    mats = make_mats(args)
+    # the oracle times the n = 256 matrices of the sweep (a bounded sample)
+    small = [(n, f) for n, f in sweep(args) if n == 256] or sweep(args)[:1]
+    mats = []
+    for n, f in small:
+        sp = gen.workload_projection(n, f)
+        mats.append({"n": n, "f": f, "k": sp["k"], "W": sp["W"]})
     import importlib
     importlib.import_module("oracle.build").build()
     import oracle
@@ -463,13 +484,8 @@ def main():
     ck = clocks.stop()
     sdpgpu.prof_enable(False)
     prof = sdpgpu.prof_get()
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    per_rank = len(mats) * args.steps
-    value = per_rank * world / (total_ms / 1000.0)
+    total_ms = max_over_ranks(dist, sum(step_ms), "cuda")
+    value = whole_job_rate(len(mats) * args.steps, world, total_ms)
     launches = sum(v["launches"] for v in prof.values())
     # roofline of the dominant kernel family (largest summed event time)
     dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
