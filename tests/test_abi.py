@@ -46,3 +46,43 @@ def test_host_only_calls(lib):
     assert abs(s.mode_frac - 1 / 3) < 1e-15 and abs(s.expand_frac - 1 / 50) < 1e-15
     assert sdpgpu.status_str(1) == "SOLVED" and sdpgpu.status_str(-4) == "E_NUMERICAL"
     assert sdpgpu.footprint_bytes(64, 64, 64) > 0
+
+
+# (size in bytes, floating point?) of the C types the header uses
+C_TYPES = {"double": (8, True), "int": (4, False), "unsigned long long": (8, False), "long long": (8, False)}
+
+
+def header_structs():
+    """(name -> [(C type, field)]) of the typedef'd structs of the header."""
+    text = open(os.path.join(ROOT, "include", "sdpgpu.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for m in re.finditer(r"typedef struct \{(.*?)\}\s*(\w+);", text, flags=re.S):
+        fields = []
+        for decl in m.group(1).split(";"):
+            decl = " ".join(decl.split())
+            if not decl:
+                continue
+            ctype, names = re.match(r"(unsigned long long|long long|double|int)\s+(.*)", decl).groups()
+            fields += [(ctype, nm.strip()) for nm in names.split(",")]
+        out[m.group(2)] = fields
+    return out
+
+
+def test_ctypes_mirrors_match_the_header():
+    """Field names, order and types of the ctypes structures equal the C
+    structs of include/sdpgpu.h (a drift would shift every later field)."""
+    import ctypes
+    from paper_1912_02767_gb300 import sdpgpu
+    hs = header_structs()
+    for cname, py in [("sdp_settings", sdpgpu.Settings), ("sdp_info", sdpgpu.Info),
+                      ("sdp_proj_info", sdpgpu.ProjInfo), ("sdp_prof_entry", sdpgpu.ProfEntry)]:
+        want = [(f,) + C_TYPES[t] for t, f in hs[cname]]
+        got = [(f, ctypes.sizeof(t), t in (ctypes.c_double, ctypes.c_float)) for f, t in py._fields_]
+        assert got == want, (cname, got, want)
+
+
+def test_default_rayleigh_ritz_settings(lib):
+    from paper_1912_02767_gb300 import sdpgpu
+    s = sdpgpu.settings()
+    assert s.rr_method == 0 and s.rr_fp32 == 0 and s.precision == sdpgpu.PREC_FP64
