@@ -93,8 +93,9 @@ def test_projection_sweep_sizes(sdp, n, f):
 
 @pytest.mark.parametrize("n,f", [(300, 0.2), (1024, 0.05)])
 def test_projection_mixed_precision(sdp, n, f):
-    """Mixed path (FP32 Grams / Rayleigh-Ritz, FP64 residual norms): the error
-    against the closed form is reported and bounded by the FP32 level."""
+    """Mixed path (split-BF16 x3 products on the tensor cores, FP32 Grams,
+    FP64 Rayleigh-Ritz and residual norms): the error against the closed
+    form is bounded by the FP32 level."""
     sp = gen.random_spectrum(n, f, np.random.default_rng(77 + n))
     ctx = sdp.Context(precision=sdp.PREC_BF16X3)
     nW = np.linalg.norm(sp["W"])
