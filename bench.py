@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--workload", default="sweep", choices=["sweep", "maxcut64", "theta500", "batch", "serve"],
                     help="sweep: the projection sweep (the bench line); the others time ADMM solves")
     ap.add_argument("--count", type=int, default=64, help="instances (batch) or requests (serve)")
+    ap.add_argument("--serve-seconds", type=float, default=0.0,
+                    help="serve: stop after this wall time and report the requests completed so far "
+                         "(0: run every request to completion)")
     ap.add_argument("--rr", type=int, default=0, choices=[0, 1],
                     help="Rayleigh-Ritz eigensolver: 0 tridiagonal where it fits (default), 1 Jacobi")
     ap.add_argument("--rr-prec", default="fp32", choices=["fp32", "fp64"],
@@ -379,6 +382,8 @@ def run_admm(args):
                       flush=True)
             if a == 0 and q == 0 and not pending:
                 break
+            if args.serve_seconds > 0 and now > args.serve_seconds:
+                break
             if a == 0 and q == 0 and pending:
                 time.sleep(max(0.0, min(0.05, pending[0][1][0] - now)))
         lat = np.array([done_t[i][0] - arrive[i] for i in done_t])
@@ -389,8 +394,10 @@ def run_admm(args):
             st[k] = st.get(k, 0) + 1
         pinf_ok = sum(1 for i in done_t if reqs[i][1].meta.get("family") == "pinf"
                       and done_t[i][1] == sdpgpu.SDP_PRIMAL_INFEASIBLE)
-        out.update({"requests": len(reqs), "solves_per_s": len(done_t) / wall, "p50_s": float(np.percentile(lat, 50)),
-                    "p99_s": float(np.percentile(lat, 99)), "statuses": st,
+        out.update({"requests": len(reqs), "completed": len(done_t), "unfinished": len(reqs) - len(done_t),
+                    "time_limit_s": args.serve_seconds or None, "solves_per_s": len(done_t) / wall,
+                    "p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
+                    "p99_s": float(np.percentile(lat, 99)) if len(lat) else None, "statuses": st,
                     "infeasible_detected": pinf_ok,
                     "infeasible_total": sum(1 for r in reqs if r[1].meta.get("family") == "pinf"),
                     "arrival_rate_per_s": 50.0, "wall_s": wall})
