@@ -38,8 +38,6 @@ template <bool TA, bool TB, typename TC>
 __global__ void k_gemm(const GemmJob* jobs, WorkMap wm);
 __global__ void k_gram_reduce(const GemmJob* jobs, WorkMap wm, int symmetrize);
 template <typename T>
-__global__ void k_rayleigh_ritz(Inst* insts, const int* list);
-template <typename T>
 __global__ void k_rr_smem(Inst* insts, const int* list, int u_global, int p_launch);
 // largest trial subspace k_rr_smem<T> holds with both p x p workspaces in
 // shared memory (2 p^2 elements of T <= 200 KiB), and with one of them

@@ -121,12 +121,10 @@ __global__ void k_gram_reduce(const GemmJob* jobs, WorkMap wm, int symmetrize) {
 }
 
 // ---------------------------------------------------------------------------
-// Rayleigh-Ritz (Algorithm 2) on a trial subspace S of width p, given its
-// Gram matrix G = S^T S and M = S^T A S (p x p, leading dimension p):
-//   L = chol(G), Linv = L^{-1}, H = Linv M Linv^T, (Theta, U) = eig(H)
-//   ascending, Coef = Linv^T U[:, top keep]; the Ritz vectors are S Coef.
-// This is Rayleigh-Ritz with Cholesky-QR orthonormalisation (Q = S L^{-T})
-// written without forming Q.  One CTA per instance; T is the arithmetic.
+// Cyclic Jacobi on one CTA (round-robin pairs, thresholds of RRConst<T>):
+// the eigensolver of the allocation-free projection below.  Rayleigh-Ritz
+// (Algorithm 2) itself is k_rr_smem (Jacobi comparator) in this file and
+// k_rr_tri / rr_wide (tridiagonal route) in rr_tri.cu / rr_wide.cu.
 // ---------------------------------------------------------------------------
 template <typename T>
 struct RRConst;
@@ -241,109 +239,6 @@ __device__ int cta_jacobi(int p, double* H, int ldh, double* U, int ldu, double*
   return sweep + 1;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(1024) k_rayleigh_ritz(Inst* insts, const int* list) {
-  const int ii = list[blockIdx.x];
-  const Inst& I = insts[ii];
-  Ctl* ctl = I.ctl;
-  const int p = ctl->p, keep = ctl->keep;
-  double *G = I.G, *M = I.M, *L = I.Linv, *H = I.H, *U = I.U;
-  extern __shared__ double dyn[];
-  double* shc = dyn;
-  double* shs = dyn + (p / 2 + 1);
-  int* sha = (int*)(dyn + 2 * (p / 2 + 1));
-  int* shb = sha + (p / 2 + 1);
-  __shared__ double red[32];
-  __shared__ int fail;
-  if (threadIdx.x == 0) fail = 0;
-  __syncthreads();
-  // 1. Cholesky of G in place (lower triangle), column by column
-  for (int j = 0; j < p; ++j) {
-    if (threadIdx.x == 0) {
-      T d = (T)G[idx2(j, j, p)];
-      if (!(d > (T)(I.prec != 0 ? 1e-6 : RRConst<T>::piv_min))) fail = j + 1;
-      else G[idx2(j, j, p)] = (double)sqrt(d);
-    }
-    __syncthreads();
-    if (fail) break;
-    T ljj = (T)G[idx2(j, j, p)];
-    for (int i = j + 1 + threadIdx.x; i < p; i += blockDim.x) G[idx2(i, j, p)] = (double)((T)G[idx2(i, j, p)] / ljj);
-    __syncthreads();
-    int w = p - j - 1;
-    for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
-      int r = t % w, c = t / w;
-      if (r < c) continue;
-      int i = j + 1 + r, k = j + 1 + c;
-      G[idx2(i, k, p)] = (double)((T)G[idx2(i, k, p)] - (T)G[idx2(i, j, p)] * (T)G[idx2(k, j, p)]);
-    }
-    __syncthreads();
-  }
-  if (fail) {
-    if (threadIdx.x == 0) ctl->rr_fail = fail;
-    return;
-  }
-  // 2. Linv = L^{-1}: one thread per column, forward substitution
-  for (int c = threadIdx.x; c < p; c += blockDim.x) {
-    for (int i = 0; i < c; ++i) L[idx2(i, c, p)] = 0.0;
-    for (int i = c; i < p; ++i) {
-      T acc = (i == c) ? (T)1 : (T)0;
-      for (int k = c; k < i; ++k) acc -= (T)G[idx2(i, k, p)] * (T)L[idx2(k, c, p)];
-      L[idx2(i, c, p)] = (double)(acc / (T)G[idx2(i, i, p)]);
-    }
-  }
-  __syncthreads();
-  // 3. H = Linv M Linv^T  (G reused for T = Linv M)
-  for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
-    int i = t % p, j = t / p;
-    T acc = 0;
-    for (int k = 0; k <= i; ++k) acc += (T)L[idx2(i, k, p)] * (T)M[idx2(k, j, p)];
-    G[idx2(i, j, p)] = (double)acc;
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
-    int i = t % p, j = t / p;
-    if (i < j) continue;
-    T acc = 0;
-    for (int k = 0; k <= j; ++k) acc += (T)G[idx2(i, k, p)] * (T)L[idx2(j, k, p)];
-    H[idx2(i, j, p)] = (double)acc;
-    H[idx2(j, i, p)] = (double)acc;
-  }
-  __syncthreads();
-  // 4. eigendecomposition of H
-  int sw = cta_jacobi<T>(p, H, p, U, p, shc, shs, sha, shb, red);
-  __syncthreads();
-  // 5. ascending order of the Ritz values (rank sort); M reused for order
-  int* ord = (int*)M;
-  for (int i = threadIdx.x; i < p; i += blockDim.x) {
-    double li = H[idx2(i, i, p)];
-    int rank = 0;
-    for (int j = 0; j < p; ++j) {
-      double lj = H[idx2(j, j, p)];
-      rank += rank_before((double)lj, j, (double)li, i);
-    }
-    ord[rank] = i;
-  }
-  __syncthreads();
-  // 6. Coef = Linv^T U[:, top keep], theta = top keep Ritz values
-  for (int t = threadIdx.x; t < p * keep; t += blockDim.x) {
-    int i = t % p, j = t / p;
-    int col = ord[p - keep + j];
-    T acc = 0;
-    for (int k = i; k < p; ++k) acc += (T)L[idx2(k, i, p)] * (T)U[idx2(k, col, p)];
-    I.Coef[idx2(i, j, p)] = (double)acc;
-  }
-  for (int j = threadIdx.x; j < keep; j += blockDim.x) I.theta[j] = H[idx2(ord[p - keep + j], ord[p - keep + j], p)];
-  if (threadIdx.x == 0) {
-    int np = 0, bad = 0;
-    for (int j = 0; j < p; ++j) {
-      np += H[idx2(j, j, p)] > 0.0;
-      bad |= !isfinite(H[idx2(j, j, p)]);
-    }
-    ctl->npos_rr = np;
-    ctl->rr_fail = bad ? -3 : 0;  // non-finite Ritz values: breakdown
-    ctl->sweeps += sw;
-  }
-}
 
 // ---------------------------------------------------------------------------
 // Residuals of Algorithm 3: R = A X - X Theta (fresh columns: Theta = 0)
@@ -492,8 +387,6 @@ template __global__ void k_gemm<false, true, double>(const GemmJob*, WorkMap);
 template __global__ void k_gemm<false, false, float>(const GemmJob*, WorkMap);
 template __global__ void k_gemm<true, false, float>(const GemmJob*, WorkMap);
 template __global__ void k_gemm<false, true, float>(const GemmJob*, WorkMap);
-template __global__ void k_rayleigh_ritz<double>(Inst*, const int*);
-template __global__ void k_rayleigh_ritz<float>(Inst*, const int*);
 
 }  // namespace sdpg
 
@@ -571,11 +464,12 @@ extern "C" int sdp_project_psd_noalloc(int n, const double* W, double* out, void
 
 namespace sdpg {
 // ---------------------------------------------------------------------------
-// Rayleigh-Ritz for small trial subspaces with every matrix in shared
-// memory (one CTA per instance): the same steps as k_rayleigh_ritz --
-// Cholesky of G, L^{-1}, H = L^{-1} M L^{-T}, parallel cyclic Jacobi, sort,
-// Coef = L^{-T} U_top -- without global-memory round trips inside the
-// Jacobi rounds.  Capacity: 2 p^2 elements of T in shared memory.
+// Rayleigh-Ritz (Algorithm 2) with Cholesky-QR orthonormalisation
+// (Q = S L^{-T}, never formed), one CTA per instance, by cyclic Jacobi: the
+// comparator of the tridiagonal route (rr_method = 1).  Cholesky of G,
+// L^{-1}, H = L^{-1} M L^{-T}, parallel cyclic Jacobi, sort,
+// Coef = L^{-T} U_top; the matrices stay in shared memory (mode 0: both,
+// mode 1: one) or in the instance's global scratch (mode 2).
 // ---------------------------------------------------------------------------
 // Dynamic shared memory: [A: p*p T][B: p*p T] (as the mode keeps them)
 // followed by the per-round rotation table and the sort order
