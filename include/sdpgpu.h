@@ -57,9 +57,10 @@ typedef enum {
  * infeasibility tests are FP64 in every mode. */
 typedef enum {
   SDP_PREC_FP64 = 0,    /* every product, Gram and Rayleigh-Ritz in FP64 (CUDA cores)          */
-  SDP_PREC_BF16X3 = 1,  /* W*S on tcgen05 tensor cores with split-BF16 x3, FP32 accumulate; Grams,  */
-                        /* block update and reconstruction in FP32; Rayleigh-Ritz in FP64 (FP32 by   */
-                        /* the rr_fp32 setting); residual norms, ADMM state and tests FP64            */
+  SDP_PREC_BF16X3 = 1,  /* W*S on tcgen05 tensor cores with split-BF16 x3, FP32 accumulate; block     */
+                        /* update and reconstruction in FP32; Rayleigh-Ritz with its Grams and       */
+                        /* Cholesky-QR in FP64 (FP32 by the rr_fp32 setting); residual norms, ADMM   */
+                        /* state and tests FP64                                                      */
   SDP_PREC_AUTO = 2     /* accepted; computes as SDP_PREC_BF16X3 (no tolerance-driven switch yet) */
 } sdp_precision;
 
@@ -85,10 +86,15 @@ typedef struct {
                        /* Sturm bisection, inverse iteration) on one CTA while the p x p  */
                        /* matrix fits its shared memory, across the GPU above; 1 cyclic    */
                        /* Jacobi at every width (comparator)              default 0     */
-  int rr_fp32;         /* 1: with BF16X3, Rayleigh-Ritz (Cholesky-QR + eigensolver) in     */
-                       /* FP32 instead of FP64 -- only for spectra whose kept eigenvalues  */
-                       /* are not small against ||W|| (e.g. a standalone projection with a */
-                       /* gap at zero); ADMM near a rank change needs FP64   default 0     */
+  int rr_fp32;         /* 1: with BF16X3, Rayleigh-Ritz (Grams, Cholesky-QR, eigensolver)  */
+                       /* in FP32 instead of FP64 -- only for spectra whose kept           */
+                       /* eigenvalues are not small against ||W|| (e.g. a standalone       */
+                       /* projection with a gap at zero); ADMM near a rank change needs    */
+                       /* FP64                                               default 0     */
+  int proj_neg;        /* sdp_project_psd only: 0 positive mode (V_warm approximates the  */
+                       /* eigenvectors of the positive eigenvalues of W); 1 negative mode  */
+                       /* (Section 5: V_warm approximates those of the negative ones;     */
+                       /* LOBPCG runs on -W and Pi(W) = W + Pi(-W))          default 0     */
 } sdp_settings;
 
 typedef struct {
@@ -103,6 +109,7 @@ typedef struct {
   int expansions;      /* random block expansions (Algorithm 3)            */
   int rank;            /* positive Ritz values at the last projection      */
   double solve_ms;     /* wall time of the solve (host clock)              */
+  int n_neg;           /* LOBPCG projections done in negative mode         */
 } sdp_info;
 
 typedef struct {
@@ -115,6 +122,8 @@ typedef struct {
   double res_fro;      /* ||R_+||_F over the positive Ritz pairs: Thm 3 gives */
                        /* ||Pi~ - Pi||_F <= sqrt(2)*res_fro (+ the perp term) */
   int jacobi_sweeps;   /* Jacobi sweeps summed over the Rayleigh-Ritz steps  */
+  int mode;            /* 0 positive, 1 negative mode; 2 the exact fallback  */
+                       /* (Cholesky-QR breakdown or block capacity)           */
 } sdp_proj_info;
 
 /* Fill *s with the defaults listed above. */
@@ -235,18 +244,33 @@ void sdp_destroy(sdp_ctx* ctx);
  * that every GPU loading the library keeps until the process exits.
  *  - n > SDP_NOALLOC_MAX_N (or n < 1, NULL pointers): SDP_E_INVALID,
  *    nothing launched.
- *  - The first call on a device looks up that device's address of the
- *    scratch array (cudaGetSymbolAddress); make that first call before any
+ *  - Every call looks up the current device's address of the scratch
+ *    array (cudaGetSymbolAddress); the first call on a device may load the
+ *    library's device code there, so make that first call before any
  *    stream capture begins.
  *  - Every call shares the one scratch array: calls that overlap on the
  *    GPU (different streams or host threads) race; serialise them.
+ *  - W may equal out (in place): the kernel copies W into the scratch
+ *    before it writes out.
  *  - Asynchronous: returns after the launch (SDP_OK, or SDP_E_CUDA when
- *    the launch failed); synchronise the stream before reading `out`. */
+ *    this call's launch failed; an error left pending by earlier work is
+ *    neither reported nor cleared); synchronise the stream before reading
+ *    `out`. */
 #define SDP_NOALLOC_MAX_N 128
 int sdp_project_psd_noalloc(int n, const double* W, double* out, void* cuda_stream);
 
 /* Text of the last CUDA error seen by this thread (static storage). */
 const char* sdp_last_error(void);
+
+/* Limit, in seconds, of every bounded device wait of the library: the
+ * tensor-core pipeline waits of the block product and the grid barriers of
+ * the cooperative Rayleigh-Ritz and Jacobi kernels.  A wait that reaches it
+ * gives up, the kernel skips the rest of its work after its own copies and
+ * MMAs in flight have finished, and the call returns SDP_E_TIMEOUT with the
+ * context still usable.  0 restores the default (2 s).  Process-wide; meant
+ * for tests of the give-up path.  Errors: SDP_E_INVALID (negative or above
+ * 60 s). */
+int sdp_set_wait_limit(double seconds);
 
 /* ---- instrumentation (no counterpart in the paper) ----------------------
  * Per kernel family: launches, device time between CUDA events recorded on

@@ -43,7 +43,8 @@ class _Settings(C.Structure):
 class _Info(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("obj", C.c_double), ("r_prim", C.c_double),
                 ("r_dual", C.c_double), ("n_exact", C.c_int), ("n_lobpcg", C.c_int),
-                ("lobpcg_steps", C.c_int), ("expansions", C.c_int), ("last_rank", C.c_int)]
+                ("lobpcg_steps", C.c_int), ("expansions", C.c_int), ("last_rank", C.c_int),
+                ("n_neg", C.c_int)]
 
 
 def lib():

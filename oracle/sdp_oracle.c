@@ -716,6 +716,7 @@ typedef struct {
   int status, iters;
   double obj, r_prim, r_dual;
   int n_exact, n_lobpcg, lobpcg_steps, expansions, last_rank;
+  int n_neg;               /* LOBPCG projections done in negative mode (on -W) */
 } orc_info;
 
 #define MODE_POS 0
@@ -808,6 +809,7 @@ int orc_admm_solve(int n, const double* C, const orc_cons* A, const double* b, c
       if (rc == ORC_OK) {
         mblk = mm;
         info->n_lobpcg++;
+        if (mode == MODE_NEG) info->n_neg++;
         info->lobpcg_steps += li[0];
         info->expansions += li[1];
         /* reconstruction: POS Z = sum theta x x^T ; NEG Z = W + sum theta x x^T */

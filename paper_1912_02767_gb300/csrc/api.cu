@@ -40,6 +40,16 @@ extern "C" const char* sdp_last_error(void) { return g_err; }
 
 static const int TPB = 256;
 
+// Limit of every bounded device wait, in nanoseconds (0: the kernels' own
+// default).  Set only by sdp_set_wait_limit, for tests of the give-up path.
+static unsigned long long g_wait_limit_ns = 0;
+extern "C" int sdp_set_wait_limit(double seconds) {
+  if (!(seconds >= 0.0) || seconds > 60.0) return SDP_E_INVALID;
+  g_wait_limit_ns = (unsigned long long)(seconds * 1e9);
+  if (seconds > 0.0 && g_wait_limit_ns == 0) g_wait_limit_ns = 1;
+  return SDP_OK;
+}
+
 namespace sdpg {
 Prof& prof() {
   static Prof P;
@@ -94,6 +104,7 @@ extern "C" void sdp_default_settings(sdp_settings* s) {
   s->seed = 0;
   s->rr_method = 0;
   s->rr_fp32 = 0;
+  s->proj_neg = 0;
 }
 
 extern "C" const char* sdp_status_str(int s) {
@@ -118,7 +129,7 @@ extern "C" const char* sdp_status_str(int s) {
 static bool settings_ok(const sdp_settings* s) {
   return s->rho > 0 && s->sigma > 0 && s->alpha > 0 && s->alpha < 2 && s->eps_abs >= 0 && s->eps_rel >= 0 &&
          s->max_iter >= 1 && s->check_every >= 1 && s->lobpcg_max_iter >= 1 && s->precision >= 0 &&
-         s->precision <= 2 && (s->rr_method == 0 || s->rr_method == 1) && (s->rr_fp32 == 0 || s->rr_fp32 == 1) && s->tol_coef > 0 && s->expand_frac > 0 && s->mode_frac > 0 && s->mode_frac <= 0.5;
+         s->precision <= 2 && (s->rr_method == 0 || s->rr_method == 1) && (s->rr_fp32 == 0 || s->rr_fp32 == 1) && (s->proj_neg == 0 || s->proj_neg == 1) && s->tol_coef > 0 && s->expand_frac > 0 && s->mode_frac > 0 && s->mode_frac <= 0.5;
 }
 
 // ---------------------------------------------------------------------------

@@ -38,6 +38,18 @@ __device__ __forceinline__ bool rank_before(double lj, int j, double li, int i) 
 }
 
 // Per-instance control block (device memory, read back by the host).
+// Bounded device waits give up after this much elapsed time (globaltimer
+// nanoseconds) unless a shorter limit is set for a test of the expiry path.
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+// Clean-up waits after a give-up (outstanding copies and MMAs must finish
+// before a CTA releases its shared and tensor memory) use this limit.
+constexpr unsigned long long kDrainLimitNs = 4000000000ull;
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 struct Ctl {
   int mode;      // projection mode of the current ADMM iteration
   int m;         // LOBPCG block width
@@ -125,7 +137,7 @@ struct Inst {
   Check* chk;
   double* chk_part;     // per-CTA partials of the check
   int prec;             // sdp_precision
-  int pad1;
+  int gram32;           // 1: the Grams S^T S, S^T A S are formed in FP32 (rr_fp32), else FP64
 };
 
 // State of a grid-wide barrier and of the cooperative kernels using it.
@@ -133,10 +145,11 @@ struct GridBar {
   unsigned count, gen;
   unsigned top;        // groups arrived (two-level barrier)
   unsigned grp[64];    // CTAs arrived per group of 16
-  int err;     // a barrier wait gave up (bounded spin)
+  int err;     // a barrier wait gave up (bounded wait)
   int fail;    // Cholesky breakdown column (1-based), 0 if none
   int sweeps;  // Jacobi sweeps done
   int pad;
+  unsigned long long limit_ns;  // wait limit of gbar (0: kWaitLimitNs)
   double fro2; // ||H||_F^2
   int rot[64]; // rotations per sweep
 };

@@ -1,8 +1,8 @@
 // gridbar.cuh -- bounded grid-wide barrier of the cooperative kernels:
 // generation counter with two-level arrival (CTAs in groups of 16, the last
 // of each group at the top, the last group bumps the generation); every
-// wait is bounded (about a second), after which GridBar::err is set and
-// every caller returns false.  Data written by other CTAs before a barrier
+// wait is bounded in time (GridBar::limit_ns, else kWaitLimitNs), after
+// which GridBar::err is set and every caller returns false.  Data written by other CTAs before a barrier
 // must be read after it past L1 (__ldcg): L1 is not coherent across SMs.
 #pragma once
 #include "common.cuh"
@@ -33,9 +33,10 @@ __device__ __forceinline__ bool gbar(GridBar* b) {
       }
     }
     if (!last) {
-      unsigned long long spins = 0;
+      const unsigned long long lim = b->limit_ns ? b->limit_ns : kWaitLimitNs;
+      const unsigned long long t0 = globaltimer_ns();
       while (*vgen == gen0) {
-        if (++spins > (1ull << 24)) {
+        if (*(volatile int*)&b->err || globaltimer_ns() - t0 > lim) {
           atomicExch(&b->err, 1);
           ok = 0;
           break;

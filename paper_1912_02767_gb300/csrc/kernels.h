@@ -117,8 +117,10 @@ int block_jacobi(cudaStream_t s, double* H, int ldh, double* U, int ldu, int p, 
                  const double* fro2_dev, int max_sweeps, double* Q, double* offp, double* offh);
 
 // tc_gemm.cu (host wrappers)
+// *err: 0 untouched; 1 a bounded wait gave up; 2 a clean-up wait gave up too
 int tc_wprod(cudaStream_t s, const void* whi, const void* wlo, int ldw, const void* bhi, const void* blo, int ldb,
-             int n, int N, double alpha, double* out, int ldo, float* part, int* err, int num_sms);
+             int n, int N, double alpha, double* out, int ldo, float* part, int* err, int num_sms,
+             unsigned long long limit_ns);
 void split_bf16(cudaStream_t s, const double* src, int lds, int rows, int cols, void* hi, void* lo, int ldd);
 
 }  // namespace sdpg

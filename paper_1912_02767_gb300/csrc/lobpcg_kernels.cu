@@ -406,8 +406,6 @@ template __global__ void k_gemm<false, true, float>(const GemmJob*, WorkMap);
 // G = I needs no Cholesky, and the eigendecomposition of M = W by the
 // CTA-wide Jacobi gives Pi(W) = sum over lambda_k > 0 of lambda_k u_k u_k^T.
 // ---------------------------------------------------------------------------
-#include <mutex>
-
 #include "../../include/sdpgpu.h"
 
 namespace sdpg {
@@ -438,27 +436,28 @@ __global__ void __launch_bounds__(1024) k_project_small_noalloc(int n, const dou
 }
 }  // namespace sdpg
 
-static std::mutex g_noalloc_mu;
-static void* g_noalloc_ptr[64];
-static bool g_noalloc_ready[64];
-
 extern "C" int sdp_project_psd_noalloc(int n, const double* W, double* out, void* cuda_stream) {
   if (n < 1 || n > SDP_NOALLOC_MAX_N || !W || !out) return SDP_E_INVALID;
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SDP_E_CUDA;
+  // host code must not use the array's name as a device address: ask the
+  // runtime for the current device's address of the array on every call
+  // (cheap after the first call on a device, which may load the module; a
+  // per-process cache would go stale after a device reset)
   void* scratch = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ready[dev]) {
-      // host code must not use the array's name as a device address: ask
-      // the runtime for this device's address of the array, once per device
-      if (cudaGetSymbolAddress(&g_noalloc_ptr[dev], sdpg::g_noalloc_scratch) != cudaSuccess) return SDP_E_CUDA;
-      g_noalloc_ready[dev] = true;
-    }
-    scratch = g_noalloc_ptr[dev];
+  if (cudaGetSymbolAddress(&scratch, sdpg::g_noalloc_scratch) != cudaSuccess) {
+    cudaGetLastError();  // consume this call's own error
+    return SDP_E_CUDA;
   }
-  sdpg::k_project_small_noalloc<<<1, 1024, 0, (cudaStream_t)cuda_stream>>>(n, W, out, (double*)scratch);
-  return cudaGetLastError() == cudaSuccess ? SDP_OK : SDP_E_CUDA;
+  // the launch's own status (an error left pending by earlier, unrelated
+  // work is neither reported nor cleared here)
+  double* sp = (double*)scratch;
+  void* args[] = {(void*)&n, (void*)&W, (void*)&out, (void*)&sp};
+  const cudaError_t e = cudaLaunchKernel((const void*)sdpg::k_project_small_noalloc, dim3(1), dim3(1024), args, 0,
+                                         (cudaStream_t)cuda_stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return SDP_E_CUDA;
+  }
+  return SDP_OK;
 }
 
 
@@ -509,7 +508,7 @@ __global__ void __launch_bounds__(1024) k_rr_smem(Inst* insts, const int* list, 
   for (int j = 0; j < p; ++j) {
     if (tid == 0) {
       T d = A[j + j * p];
-      if (!(d > (T)(I.prec != 0 ? 1e-6 : RRConst<T>::piv_min))) fail = j + 1;
+      if (!(d > (T)(I.gram32 ? 1e-6 : RRConst<T>::piv_min))) fail = j + 1;
       A[j + j * p] = sqrt(d > (T)0 ? d : (T)1);
     }
     __syncthreads();

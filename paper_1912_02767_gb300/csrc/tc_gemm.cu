@@ -12,8 +12,12 @@
 // reads TMEM with tcgen05.ld.  Split-K over blockIdx.z spreads a single
 // large product over all SMs; partials are reduced in a second kernel.
 //
-// Every mbarrier wait is bounded; on expiry the kernel records the error
-// in *err and skips the rest of its work.
+// Every mbarrier wait is bounded in time (TcParams::limit_ns, else
+// kWaitLimitNs); on expiry the kernel records the error in *err and skips
+// the rest of its work, but before the CTA releases its tensor memory it
+// still waits (bounded by kDrainLimitNs) for the MMAs it issued and the
+// producer waits for the TMA loads it issued, so no asynchronous copy or
+// MMA outlives the CTA's shared or tensor memory.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -27,7 +31,6 @@ namespace sdpg {
 static constexpr int TC_BM = 128;
 static constexpr int TC_BK = 64;                       // bf16 elements per 128-byte row
 static constexpr int TC_A_BYTES = TC_BM * TC_BK * 2;   // 16 KiB
-static constexpr long long TC_WAIT_LIMIT = 1LL << 26;  // ~ a second of polling
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -46,14 +49,26 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait: false when the limit expired or another thread aborted
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
-  for (long long it = 0; it < TC_WAIT_LIMIT; ++it) {
+// bounded wait: false when `limit_ns` of elapsed time passed (the wait then
+// raises the CTA's abort flag) or another thread of the CTA aborted
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          unsigned long long limit_ns) {
+  const unsigned long long t0 = globaltimer_ns();
+  while (true) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort_flag) return false;
+    if (globaltimer_ns() - t0 > limit_ns) {
+      *abort_flag = 1;
+      return false;
+    }
   }
-  *abort_flag = 1;
-  return false;
+}
+// clean-up wait after an abort: ignores the abort flag
+__device__ __forceinline__ bool mbar_drain(uint64_t* bar, uint32_t parity) {
+  const unsigned long long t0 = globaltimer_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (globaltimer_ns() - t0 > kDrainLimitNs) return false;
+  return true;
 }
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
   asm volatile(
@@ -105,6 +120,7 @@ struct TcParams {
   int ldo;
   float* part;        // FP32 partials: part[(s*N + col)*M + row] when splits > 1
   int* err;
+  unsigned long long limit_ns;  // wait limit (0: kWaitLimitNs)
 };
 
 __global__ void __launch_bounds__(128, 1) k_tc_wprod(const __grid_constant__ CUtensorMap mWhi,
@@ -147,12 +163,15 @@ __global__ void __launch_bounds__(128, 1) k_tc_wprod(const __grid_constant__ CUt
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
 
+  const unsigned long long lim = P.limit_ns ? P.limit_ns : kWaitLimitNs;
+  bool drained = true;
   if (nkt > 0) {
     if (warp == 0 && lane == 0) {
       // TMA producer
+      int issued = 0;
       for (int it = 0; it < nkt; ++it) {
         const int s = it % stages;
-        if (it >= stages && !mbar_wait(&empty_bar[s], ((it / stages) - 1) & 1, &abort_flag)) break;
+        if (it >= stages && !mbar_wait(&empty_bar[s], ((it / stages) - 1) & 1, &abort_flag, lim)) break;
         uint8_t* st = smem + (size_t)s * stage_bytes;
         mbar_expect_tx(&full_bar[s], (uint32_t)stage_bytes);
         const int kx = (kt0 + it) * TC_BK;  // multiple of 64 elements = 128 bytes
@@ -160,13 +179,18 @@ __global__ void __launch_bounds__(128, 1) k_tc_wprod(const __grid_constant__ CUt
         tma_load_2d(st + TC_A_BYTES, &mWlo, &full_bar[s], kx, m0);
         tma_load_2d(st + 2 * TC_A_BYTES, &mBhi, &full_bar[s], kx, n0);
         tma_load_2d(st + 2 * TC_A_BYTES + b_bytes, &mBlo, &full_bar[s], kx, n0);
+        issued = it + 1;
       }
+      // the last load issued into each stage completes its latest phase
+      // whether or not the MMA side consumed it: wait for all of them
+      for (int it = (issued > stages ? issued - stages : 0); it < issued; ++it)
+        drained &= mbar_drain(&full_bar[it % stages], (it / stages) & 1);
     } else if (warp == 1 && lane == 0) {
       // MMA issuer
       const uint32_t idesc = umma_idesc_bf16(bn);
       for (int it = 0; it < nkt; ++it) {
         const int s = it % stages;
-        if (!mbar_wait(&full_bar[s], (it / stages) & 1, &abort_flag)) break;
+        if (!mbar_wait(&full_bar[s], (it / stages) & 1, &abort_flag, lim)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         uint8_t* st = smem + (size_t)s * stage_bytes;
         const uint64_t ahi = umma_desc_sw128(st), alo = umma_desc_sw128(st + TC_A_BYTES);
@@ -184,7 +208,10 @@ __global__ void __launch_bounds__(128, 1) k_tc_wprod(const __grid_constant__ CUt
     }
     __syncwarp();
     // epilogue: every warp reads its 32 TMEM lanes (rows)
-    bool ok = mbar_wait(&done_bar, 0, &abort_flag);
+    bool ok = mbar_wait(&done_bar, 0, &abort_flag, lim);
+    // after an abort the MMAs already issued may still run: done_bar tracks
+    // them all (the issuer commits it on every exit path)
+    if (!ok) drained &= mbar_drain(&done_bar, 0);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok && !abort_flag) {
       const int row = m0 + warp * 32 + lane;
@@ -214,10 +241,12 @@ __global__ void __launch_bounds__(128, 1) k_tc_wprod(const __grid_constant__ CUt
         }
       }
     }
-    if (abort_flag && threadIdx.x == 0) atomicExch(P.err, 1);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
+  // every thread is past its drain: nothing of this CTA is in flight (or a
+  // drain itself gave up, reported as error 2)
+  const int undrained = __syncthreads_or(drained ? 0 : 1);
+  if (threadIdx.x == 0 && (abort_flag || undrained)) atomicMax(P.err, undrained ? 2 : 1);
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
@@ -288,7 +317,8 @@ static bool make_map(CUtensorMap* map, const void* base, int inner, int rows, in
 // at least 8 * n * N floats.  Returns 0, or -1 if the tensor maps could not
 // be built (nothing launched).
 int tc_wprod(cudaStream_t s, const void* whi, const void* wlo, int ldw, const void* bhi, const void* blo, int ldb,
-             int n, int N, double alpha, double* out, int ldo, float* part, int* err, int num_sms) {
+             int n, int N, double alpha, double* out, int ldo, float* part, int* err, int num_sms,
+             unsigned long long limit_ns) {
   if (n < 1 || N < 1) return 0;
   int bn = ((N + 15) / 16) * 16;
   if (bn > 256) bn = 256;
@@ -320,6 +350,7 @@ int tc_wprod(cudaStream_t s, const void* whi, const void* wlo, int ldw, const vo
   P.ldo = ldo;
   P.part = part;
   P.err = err;
+  P.limit_ns = limit_ns;
   const size_t smem = (size_t)stages * stage_bytes + 1024;
   static bool attr = false;
   if (!attr) {

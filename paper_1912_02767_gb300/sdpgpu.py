@@ -28,13 +28,13 @@ class Settings(C.Structure):
                 ("max_iter", C.c_int), ("check_every", C.c_int), ("lobpcg_max_iter", C.c_int),
                 ("precision", C.c_int), ("exact_only", C.c_int), ("tol_coef", C.c_double),
                 ("tol_exp", C.c_double), ("expand_frac", C.c_double), ("mode_frac", C.c_double),
-                ("seed", C.c_ulonglong), ("rr_method", C.c_int), ("rr_fp32", C.c_int)]
+                ("seed", C.c_ulonglong), ("rr_method", C.c_int), ("rr_fp32", C.c_int), ("proj_neg", C.c_int)]
 
 
 class Info(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("obj", C.c_double), ("r_prim", C.c_double),
                 ("r_dual", C.c_double), ("n_exact", C.c_int), ("n_lobpcg", C.c_int), ("lobpcg_steps", C.c_int),
-                ("expansions", C.c_int), ("rank", C.c_int), ("solve_ms", C.c_double)]
+                ("expansions", C.c_int), ("rank", C.c_int), ("solve_ms", C.c_double), ("n_neg", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -43,7 +43,7 @@ class Info(C.Structure):
 class ProjInfo(C.Structure):
     _fields_ = [("status", C.c_int), ("steps", C.c_int), ("m", C.c_int), ("npos", C.c_int),
                 ("expansions", C.c_int), ("converged", C.c_int), ("res_fro", C.c_double),
-                ("jacobi_sweeps", C.c_int)]
+                ("jacobi_sweeps", C.c_int), ("mode", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -96,6 +96,7 @@ def load():
     L.sdp_server_destroy.restype = None
     L.sdp_block_product.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int]
     L.sdp_project_psd_noalloc.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+    L.sdp_set_wait_limit.argtypes = [C.c_double]
     L.sdp_prof_enable.argtypes = [C.c_int]
     L.sdp_prof_enable.restype = None
     L.sdp_prof_reset.restype = None
@@ -121,6 +122,11 @@ def prof_get():
         _check(L.sdp_prof_get(f, C.byref(e)), "sdp_prof_get")
         out[name] = {"launches": e.launches, "ms": e.ms, "timed": e.timed, "flops": e.flops, "bytes": e.bytes}
     return out
+
+
+def set_wait_limit(seconds):
+    """sdp_set_wait_limit: limit of every bounded device wait (0 = default)."""
+    return load().sdp_set_wait_limit(float(seconds))
 
 
 def status_str(code):

@@ -153,3 +153,67 @@ def test_server_continuous_batching(sdp):
         rc, info = srv.poll(t)
         assert info["status"] == ref["status"] and info["iters"] == ref["iters"]
         assert abs(info["obj"] - ref["obj"]) <= 1e-9 * abs(ref["obj"])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_theta_complete_graph_negative_mode(sdp, orc, prec):
+    """theta(K_n) = 1, n = 40: the iterate W tends to the full-rank I/n, so
+    the Section 5 rule selects negative mode (LOBPCG on -W, Z = W + Pi(-W)).
+    The GPU objective equals the closed form and the oracle's, and most
+    projections ran in negative mode."""
+    n = 40
+    inst = gen.theta(n, 0.0, edges=gen.complete_edges(n))
+    kw = dict(eps_abs=1e-6, rho=1.0, tol_coef=0.1, max_iter=20000)
+    ref = orc.admm_solve(inst.n, inst.C, cons_of(orc, inst), inst.b, use_lobpcg=1, **kw)
+    p = sdp.PREC_FP64 if prec == "fp64" else sdp.PREC_BF16X3
+    _, res, X, _, _ = gpu_solve(sdp, inst, precision=p, **kw)
+    assert res["status_name"] == ref["status_name"] == "SOLVED"
+    assert res["n_neg"] > res["n_lobpcg"] // 2 and res["n_neg"] > 100, res
+    assert abs(res["obj"] - ref["obj"]) <= OBJ_TOL * abs(ref["obj"])
+    assert -res["obj"] == pytest.approx(1.0, abs=1e-5)
+
+
+def test_maxcut64_mixed_matches_oracle(sdp, orc):
+    """The mixed path (tensor-core products, FP64 Grams and Rayleigh-Ritz,
+    FP64 ADMM state) on max-cut n = 64 at residual 1e-4."""
+    inst = gen.workload_maxcut64(0)
+    ref = orc.admm_solve(inst.n, inst.C, cons_of(orc, inst), inst.b, eps_abs=1e-4)
+    c, res, X, y, S = gpu_solve(sdp, inst, eps_abs=1e-4, precision=sdp.PREC_BF16X3)
+    assert res["status_name"] == "SOLVED" == ref["status_name"]
+    assert abs(res["obj"] - ref["obj"]) <= OBJ_TOL * abs(ref["obj"])
+    assert res["n_lobpcg"] > res["n_exact"]
+    rp, rd, obj = orc.residuals(inst.n, inst.C, cons_of(orc, inst), inst.b, X, X, y, -S)
+    assert rd <= 1e-4 + 1e-12
+
+
+def test_theta_small_mixed_matches_oracle(sdp, orc):
+    """Lovasz theta n = 40 on the mixed path, compared at residual 1e-6 as in
+    the FP64 test."""
+    inst = gen.theta(40, 0.2, np.random.default_rng(13))
+    kw = dict(eps_abs=1e-6, rho=10.0, tol_coef=0.1, max_iter=40000)
+    ref = orc.admm_solve(inst.n, inst.C, cons_of(orc, inst), inst.b, use_lobpcg=1, **kw)
+    _, res, _, _, _ = gpu_solve(sdp, inst, precision=sdp.PREC_BF16X3, **kw)
+    assert res["status_name"] == ref["status_name"] == "SOLVED"
+    assert abs(res["obj"] - ref["obj"]) <= OBJ_TOL * abs(ref["obj"])
+
+
+def test_batch_mixed_matches_oracle_objectives(sdp):
+    """An uneven max-cut batch (n ~ U{64..256}) solved together on the mixed
+    path: each instance's objective against the FP64 oracle's LOBPCG-ADMM
+    objective stored by tests/golden/make_batch_objectives.py."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "batch_maxcut_objectives.json")))
+    insts = gen.workload_batch(len(gold["instances"]), 64, 256)
+    ctxs = [sdp.Context(eps_abs=1e-4, precision=sdp.PREC_BF16X3).setup(i) for i in insts]
+    infos = sdp.batch_solve(ctxs)
+    solved = 0
+    for g, inst, r in zip(gold["instances"], insts, infos):
+        assert inst.n == g["n"]
+        if g["status"] == "SOLVED":
+            assert r["status_name"] == "SOLVED", (g, r)
+            assert abs(r["obj"] - g["obj"]) <= OBJ_TOL * abs(g["obj"]), (g, r)
+            solved += 1
+        else:  # the oracle itself stops at the iteration limit (slow fixed-rho ADMM)
+            assert r["status_name"] in ("MAX_ITER", "SOLVED"), (g, r)
+    assert solved >= len(gold["instances"]) // 2

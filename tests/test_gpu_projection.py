@@ -168,3 +168,85 @@ def test_projection_repeated_eigenvalues(sdp, prec):
     P, V, info = ctx.project_psd(W, X0, tol=tol)
     assert info["npos"] == 12
     assert np.linalg.norm(P - ref) / np.linalg.norm(W) <= (TOL_FP64 if prec == "fp64" else 1e-4)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_projection_negative_mode(sdp, prec):
+    """Negative mode (Section 5, Eq. 2's second form): W with k/n = 0.8
+    positive eigenvalues; the warm block approximates the eigenvectors of the
+    negative ones, LOBPCG runs on -W (the products take alpha = -1) and the
+    reconstruction is Z = W + Pi(-W).  Closed form at the precision's level."""
+    n, k = 300, 240
+    rng = np.random.default_rng(801)
+    sp = gen.random_spectrum(n, k / n, rng)
+    Q, lam = sp["Q"], sp["lam"]
+    neg = np.where(lam < 0)[0]
+    X0 = Q[:, neg] + 1e-3 / np.sqrt(n) * rng.standard_normal((n, neg.size))
+    nW = np.linalg.norm(sp["W"])
+    p = sdp.PREC_FP64 if prec == "fp64" else sdp.PREC_BF16X3
+    ctx = sdp.Context(precision=p, proj_neg=1)
+    tol = 0.0 if prec == "fp64" else 1e-5 * nW / np.sqrt(2 * neg.size)
+    P, V, info = ctx.project_psd(sp["W"], X0, tol=tol)
+    err = np.linalg.norm(P - closed_form(sp)) / nW
+    assert info["mode"] == 1 and info["npos"] == n - k, info
+    assert err <= (TOL_FP64 if prec == "fp64" else 1e-4), err
+
+
+@pytest.mark.parametrize("n,f", [(1024, 0.25), (4096, 0.01), (4096, 0.05), (4096, 0.25)])
+def test_projection_sweep_full_size_fp64(sdp, n, f):
+    """The sweep's largest matrices in FP64 mode (products, Grams and
+    Rayleigh-Ritz FP64) against the closed form at 1e-6."""
+    sp = gen.workload_projection(n, f)
+    ctx = sdp.Context()
+    P, V, info = ctx.project_psd(sp["W"], sp["X0"])
+    assert np.linalg.norm(P - closed_form(sp)) / np.linalg.norm(sp["W"]) <= TOL_FP64
+    assert info["npos"] == sp["k"]
+
+
+@pytest.mark.parametrize("n,f", [(1024, 0.25), (4096, 0.25)])
+def test_projection_sweep_full_size_mixed(sdp, n, f):
+    """The same matrices on the mixed path (tensor-core products, FP64
+    Grams and Rayleigh-Ritz): the closed-form error stays at the split-BF16
+    product level."""
+    sp = gen.workload_projection(n, f)
+    nW = np.linalg.norm(sp["W"])
+    ctx = sdp.Context(precision=sdp.PREC_BF16X3)
+    P, V, info = ctx.project_psd(sp["W"], sp["X0"], tol=1e-5 * nW / np.sqrt(2 * sp["k"]))
+    assert np.linalg.norm(P - closed_form(sp)) / nW <= 1e-4
+    assert info["npos"] == sp["k"]
+
+
+def test_bounded_waits_give_up_and_the_context_stays_usable(sdp):
+    """A bounded device wait that reaches its limit gives up: the call
+    returns SDP_E_TIMEOUT (no trap, no hang) and, with the default limit
+    restored, the same context computes correctly.  Covered: the tcgen05
+    pipeline waits of the block product and the grid barriers of the
+    cooperative Rayleigh-Ritz kernels."""
+    torch = pytest.importorskip("torch")
+    n, k = 1024, 64
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((n, n))
+    W = 0.5 * (A + A.T)
+    B = rng.standard_normal((n, k))
+    Wd = torch.from_numpy(np.ascontiguousarray(W)).cuda()
+    Bd = torch.from_numpy(np.ascontiguousarray(B.T)).cuda()
+    ctx = sdp.Context(precision=sdp.PREC_BF16X3)
+    out = torch.zeros((k, n), dtype=torch.float64, device="cuda")
+    try:
+        assert sdp.set_wait_limit(1e-9) == 0
+        with pytest.raises(RuntimeError, match="E_TIMEOUT"):
+            ctx.block_product(Wd, Bd, out)
+        # a wide trial subspace: Rayleigh-Ritz on the whole GPU (grid barriers)
+        sp = gen.random_spectrum(600, 1 / 3, np.random.default_rng(4))
+        pctx = sdp.Context()
+        with pytest.raises(RuntimeError, match="E_TIMEOUT"):
+            pctx.project_psd(sp["W"], sp["X0"])
+    finally:
+        sdp.set_wait_limit(0.0)
+    ctx.block_product(Wd, Bd, out)
+    torch.cuda.synchronize()
+    ref = W @ B
+    assert np.linalg.norm(out.cpu().numpy().T - ref) / np.linalg.norm(ref) <= 3e-5
+    P, _, info = pctx.project_psd(sp["W"], sp["X0"])
+    assert np.linalg.norm(P - closed_form(sp)) / np.linalg.norm(sp["W"]) <= TOL_FP64
+    assert sdp.set_wait_limit(-1.0) == -1

@@ -205,3 +205,25 @@ def test_planted_mistakes_are_caught(orc):
     bad_scale.C = bad_scale.C * 2  # a dropped 1/2 somewhere
     wrong = -_solve(orc, bad_scale)["obj"]
     assert abs(good - 4.5225424859) < 2e-5 and abs(wrong - 4.5225424859) > 1.0
+
+
+def test_theta_complete_graph_runs_negative_mode(orc):
+    """theta(K_n) = 1.  Every vertex pair is an edge, so the optimal X is
+    diagonal with unit trace and the ADMM iterate W tends to the full-rank
+    I/n: more than 2n/3 of its eigenvalues are positive and the mode rule of
+    Section 5 selects negative mode (LOBPCG on -W, Z = W + Pi(-W)).  The
+    LOBPCG-ADMM objective must equal the closed form and the exact-projection
+    ADMM, and the negative branch must have carried the solve."""
+    n = 40
+    inst = gen.theta(n, 0.0, edges=gen.complete_edges(n))
+    cons = cons_of(orc, inst)
+    kw = dict(eps_abs=1e-6, rho=1.0, tol_coef=0.1, max_iter=20000)
+    ex = orc.admm_solve(n, inst.C, cons, inst.b, use_lobpcg=0, **kw)
+    lo = orc.admm_solve(n, inst.C, cons, inst.b, use_lobpcg=1, **kw)
+    assert ex["status_name"] == lo["status_name"] == "SOLVED"
+    assert lo["n_neg"] > lo["n_lobpcg"] // 2 and lo["n_neg"] > 100
+    assert abs(lo["obj"] - ex["obj"]) <= 1e-4 * abs(ex["obj"])
+    assert -lo["obj"] == pytest.approx(1.0, abs=1e-5)
+    assert -ex["obj"] == pytest.approx(1.0, abs=1e-5)
+    # the returned X is (nearly) full rank: more than 2n/3 positive eigenvalues
+    assert np.sum(np.linalg.eigvalsh(lo["x"]) > 1e-3 / n) > 2 * n // 3

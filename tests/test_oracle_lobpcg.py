@@ -88,3 +88,30 @@ def test_theorem3_bound_holds(orc, seed):
     perp = np.sum(np.maximum(ev, 0) ** 2)
     lhs = np.linalg.norm(approx - exact) ** 2
     assert lhs <= 2 * np.linalg.norm(R) ** 2 + perp + 1e-12
+
+
+def test_negative_mode_reconstruction_is_the_projection(orc):
+    """Negative mode (Section 5): with more than 2n/3 positive eigenvalues the
+    projection is computed from the positive eigenpairs of -W, Pi(W) = W +
+    Pi(-W) (Eq. 2's second form).  LOBPCG on -W from a perturbed block of
+    W's negative eigenvectors, then the reconstruction, must give the closed
+    form Q Lambda_+ Q^T (k/n = 0.8); the Moreau decomposition W = Pi(W) -
+    Pi(-W) then holds.  A sign slip (reconstructing from -W) is caught."""
+    rng = np.random.default_rng(11)
+    n, k = 90, 72
+    sp = gen.random_spectrum(n, k / n, rng)
+    W, Q, lam = sp["W"], sp["Q"], sp["lam"]
+    neg = np.where(lam < 0)[0]
+    X0 = Q[:, neg] + 1e-3 / np.sqrt(n) * rng.standard_normal((n, neg.size))
+    res = orc.lobpcg(-W, X0, tol=1e-11, maxit=50)
+    assert res["rc"] == 0 and res["converged"] and res["npos"] == n - k
+    pos = res["lam"] > 0
+    Pneg = (res["X"][:, pos] * res["lam"][pos]) @ res["X"][:, pos].T   # Pi(-W)
+    Z = W + Pneg
+    exact = (Q * np.maximum(lam, 0)) @ Q.T
+    nW = np.linalg.norm(W)
+    assert np.linalg.norm(Z - exact) <= 1e-9 * nW
+    assert np.linalg.norm((Z - Pneg) - W) <= 1e-12 * nW                 # Moreau: Pi(W) - Pi(-W) = W
+    assert np.linalg.eigvalsh(Z).min() >= -1e-9 and np.linalg.eigvalsh(-Pneg).max() <= 1e-9
+    planted = -W + Pneg                                                 # sign slip in the reconstruction
+    assert np.linalg.norm(planted - exact) > 1e-2 * nW
