@@ -55,8 +55,9 @@ def parse():
                          "Cholesky-QR (FP64 by default; fp32 only as a comparison)")
     ap.add_argument("--fp64-steps", type=int, default=None,
                     help="timed steps of the plain FP64 path beside the bench line (default: --steps)")
-    ap.add_argument("--kernel", default=None, choices=[None, "product"],
-                    help="time one kernel alone: 'product' = W B on the tensor cores (sdp_block_product)")
+    ap.add_argument("--kernel", default=None, choices=[None, "product", "dense"],
+                    help="time one kernel alone: 'product' = W B on the tensor cores (sdp_block_product); "
+                         "'dense' = the FP64-accurate split-product GEMM (sdp_dense_product), n x n x n")
     ap.add_argument("--n", type=int, default=6144)
     ap.add_argument("--k", type=int, default=256)
     ap.add_argument("--iters", type=int, default=20)
@@ -117,6 +118,43 @@ def run_product(args):
             "algorithmic_tflops": tfl, "executed_tflops": tfl * (3 if args.prec != "fp64" else 1),
             "bf16_peak_tflops": pk.get("bf16_tflops"), "rel_err_vs_fp64": err, "launches": pr["timed"],
             "bytes_per_launch": pr["bytes"] / max(pr["timed"], 1)}
+    print(json.dumps(line), flush=True)
+
+
+def run_dense(args):
+    """The FP64-accurate split-product GEMM alone (sdp_dense_product,
+    C = A^T B with A, B n x n, the Gram shape of Rayleigh-Ritz): algorithmic
+    FP64-equivalent flops 2 n^3 per launch; the tensor cores execute the 21
+    bf16 digit products, 21 x 2 n^3 flops."""
+    import torch
+    from paper_1912_02767_gb300 import build_lib, sdpgpu
+    build_lib.build()
+    sdpgpu.load()
+    n = args.n
+    g = torch.Generator(device="cuda").manual_seed(2)
+    A = torch.randn((n, n), dtype=torch.float64, device="cuda", generator=g)
+    B = torch.randn((n, n), dtype=torch.float64, device="cuda", generator=g)
+    C = torch.empty_like(A)
+    stream = torch.cuda.current_stream()
+    ctx = sdpgpu.Context(stream=stream, precision=sdpgpu.PREC_BF16X3)
+    for _ in range(3):
+        ctx.dense_product(A, B, C, trans_a=True)
+    torch.cuda.synchronize()
+    ref = B @ A.t()  # a torch tensor t holds the column-major matrix t^T: C^T = (A_cm^T B_cm)^T = t_B t_A^T
+    err = float((C - ref).abs().max() / ref.abs().max())
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.iters)]
+    for e0, e1 in evs:
+        e0.record(stream)
+        ctx.dense_product(A, B, C, trans_a=True)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in evs) / len(evs)
+    fl = 2.0 * n ** 3
+    pk = peaks()
+    line = {"kernel": "FP64-accurate split-product GEMM (sdp_dense_product, TN)", "n": n, "avg_call_ms": ms,
+            "fp64_equivalent_tflops": fl / (ms / 1e3) / 1e12, "executed_bf16_tflops": 21 * fl / (ms / 1e3) / 1e12,
+            "bf16_peak_tflops": pk.get("bf16_tflops"), "max_rel_err_vs_cublas_fp64": err, "calls": len(evs),
+            "note": "each call also slices both operands (two row-scale and two slicing kernels)"}
     print(json.dumps(line), flush=True)
 
 
@@ -201,24 +239,57 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# matrices of the sweep that the one-thread CPU oracle projects within
+# seconds (n = 256 at every k/n, n = 1024 at 1% and 5%); the rest take it
+# minutes to hours (n = 1024 at 25%: about 80 s)
+ORACLE_SAMPLE = [(256, 0.01), (256, 0.05), (256, 0.25), (1024, 0.01), (1024, 0.05)]
+
+
+def host_info():
+    """Host cores of this machine (the GPU machine's when run there)."""
+    model = None
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu model")):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return {"host_cores": os.cpu_count(), "host_cpu": model}
+
+
+def oracle_tol(m):
+    return 0.5e-6 * float(np.linalg.norm(m["W"])) / np.sqrt(2.0 * m["k"])
+
+
 def cpu_oracle_rate(mats, budget_s=12.0):
-    """The FP64 CPU oracle (cyclic Jacobi projection) on a bounded sample:
-    the sweep's n = 256 matrices, repeated until about budget_s seconds."""
+    """The FP64 CPU oracle's LOBPCG projection (Algorithm 3 + Eq. 2, one
+    thread, same warm starts and FP64 tolerance as the GPU's FP64 path) on a
+    bounded sample of the sweep: ORACLE_SAMPLE, repeated for about budget_s
+    seconds.  Returns the rate over the sample and per matrix."""
     import importlib
     importlib.import_module("oracle.build").build()
     import oracle
-    sample = [m for m in mats if m["n"] == 256] or sorted(mats, key=lambda m: m["n"])[:1]
+    sample = [m for m in mats if (m["n"], m["f"]) in ORACLE_SAMPLE] or sorted(mats, key=lambda m: m["n"])[:1]
+    per = {(m["n"], m["f"]): 0.0 for m in sample}
     done, t0 = 0, time.perf_counter()
     while True:
         for m in sample:
-            oracle.psd_project(m["W"])
+            t1 = time.perf_counter()
+            oracle.lobpcg_project(m["W"], m["X0"], oracle_tol(m))
+            per[(m["n"], m["f"])] += time.perf_counter() - t1
             done += 1
         if time.perf_counter() - t0 >= budget_s:
             break
     dt = time.perf_counter() - t0
-    return {"value": done / dt, "unit": "projections/s", "cores": 1, "kind": "oracle",
-            "sample": "%d Jacobi projections of the sweep's n=%d matrices (%d distinct), %.1f s, 1 thread"
-                      % (done, sample[0]["n"], len(sample), dt)}
+    reps = done // len(sample)
+    out = {"value": done / dt, "unit": "projections/s", "cores": 1, "kind": "oracle",
+           "sample": "oracle LOBPCG projection (FP64, one thread, tol 0.5e-6 ||W||_F / sqrt(2k)) of %d of the "
+                     "sweep's matrices (%s), %d passes, %.1f s" % (len(sample), ", ".join(
+                         "n=%d k/n=%g" % nf for nf in per), reps, dt),
+           "per_matrix": [{"n": n, "k/n": f, "projections_per_s": reps / t} for (n, f), t in per.items()]}
+    out.update(host_info())
+    return out
 
 
 def make_mats(args):
@@ -230,37 +301,41 @@ def make_mats(args):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle's LOBPCG projection (the
+    paper's method, one thread) on the sweep's bounded sample ORACLE_SAMPLE
+    per step, with the GPU arm's warm starts and FP64 tolerance; per-matrix
+    rates are printed so that the GPU line's per-matrix times can be set
+    beside them."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    # the oracle times the n = 256 matrices of the sweep (a bounded sample)
-    small = [(n, f) for n, f in sweep(args) if n == 256] or sweep(args)[:1]
-    mats = []
-    for n, f in small:
-        sp = gen.workload_projection(n, f)
-        mats.append({"n": n, "f": f, "k": sp["k"], "W": sp["W"]})
+    mats = [m for m in make_mats(args) if (m["n"], m["f"]) in ORACLE_SAMPLE] or make_mats(args)[:1]
     import importlib
     importlib.import_module("oracle.build").build()
     import oracle
-    sample = [m for m in mats if m["n"] == 256] or mats[:1]
     for _ in range(args.warmup):
-        oracle.psd_project(sample[0]["W"])
+        oracle.lobpcg_project(mats[0]["W"], mats[0]["X0"], oracle_tol(mats[0]))
+    per = [0.0] * len(mats)
     t0 = time.perf_counter()
-    done = 0
     for _ in range(args.steps):
-        for m in sample:
-            oracle.psd_project(m["W"])
-            done += 1
+        for q, m in enumerate(mats):
+            t1 = time.perf_counter()
+            oracle.lobpcg_project(m["W"], m["X0"], oracle_tol(m))
+            per[q] += time.perf_counter() - t1
     dt = time.perf_counter() - t0
-    v = done / dt
+    v = len(mats) * args.steps / dt
+    sample = ("oracle LOBPCG projection (FP64, one thread) of %d of the sweep's 9 matrices per step: %s"
+              % (len(mats), ", ".join("n=%d k/n=%g" % (m["n"], m["f"]) for m in mats)))
+    cpu = {"value": v, "unit": "projections/s", "cores": 1, "kind": "oracle", "sample": sample}
+    cpu.update(host_info())
     line = {"impl": "reference", "metric": "PSD projections/s (warm-started LOBPCG, k/n sweep)", "value": v,
             "unit": "projections/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "psd_projection_sweep", "sample": "n=256 matrices of the sweep",
-                       "matrices_per_step": len(sample)},
-            "cpu_baseline": {"value": v, "unit": "projections/s", "cores": 1, "kind": "oracle",
-                             "sample": "%d Jacobi projections of the sweep's n=256 matrices per step" % len(sample)},
+            "config": {"workload": "psd_projection_sweep", "sample": [[m["n"], m["f"]] for m in mats]},
+            "cpu_baseline": cpu,
+            "per_matrix": [{"n": m["n"], "k/n": m["f"], "projections_per_s": args.steps / per[q]}
+                           for q, m in enumerate(mats)],
             "e2e": {"value": v, "unit": "projections/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -412,6 +487,8 @@ def main():
         return run_reference(args)
     if args.kernel == "product":
         return run_product(args)
+    if args.kernel == "dense":
+        return run_dense(args)
     if args.workload != "sweep":
         return run_admm(args)
     import torch
@@ -579,6 +656,9 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_oracle_rate(mats)
+    # the GPU rate on the oracle's sample (like for like with the reference arm)
+    samp = [q for q, m in enumerate(mats) if (m["n"], m["f"]) in ORACLE_SAMPLE]
+    gpu_on_sample = (len(samp) / (sum(per_ms[q] for q in samp) / 1000.0)) if samp else None
     if rank == 0:
         line = {"metric": "PSD projections/s (warm-started LOBPCG, k/n sweep)", "value": value,
                 "unit": "projections/s", "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
@@ -592,7 +672,7 @@ def main():
                            "l2": "flushed between steps (256 MiB write)",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "fp64_path": fp64_path,
+                "fp64_path": fp64_path, "rate_on_oracle_sample": gpu_on_sample,
                 "speedup_vs_fp64_path": (value / fp64_path["value"]) if fp64_path else None,
                 "clocks": ck, "max_rel_err_vs_closed_form": max(errs),
                 "per_matrix": [{"n": m["n"], "k": m["k"], "ms": round(per_ms[q], 3), "rel_err": errs[q],

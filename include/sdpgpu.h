@@ -195,6 +195,23 @@ int sdp_project_psd(sdp_ctx* ctx, int n, const double* W, double* out, double* V
  * Errors: SDP_E_INVALID, SDP_E_NOMEM, SDP_E_CUDA. */
 int sdp_block_product(sdp_ctx* ctx, int n, const double* W, const double* B, int k, double* out, int resplit_w);
 
+/* C = alpha op(A) op(B) + beta C for FP64 column-major device arrays of the
+ * current device (op(X) = X, or X^T when trans_x != 0; op(A) is M x K,
+ * op(B) K x N), computed on the tcgen05 tensor cores to FP64 accuracy by
+ * the split-product scheme the mixed-precision Rayleigh-Ritz step uses for
+ * its Grams, H = L^{-1} M L^{-T}, Ritz coefficients and block update
+ * (Algorithm 2 inside Algorithm 3): each row of op(A) and column of op(B)
+ * is scaled by a power of two and cut into six bf16 digit planes, the 21
+ * leading digit products are accumulated exactly per 128-deep chunk, and
+ * |C - op(A)op(B)| <= K 2^-44 max_k|A_mk| max_k|B_kn| elementwise (plus the
+ * final rounding).  Inf/NaN inputs give NaN in the affected rows and
+ * columns.  Runs on the context's stream and returns after it (the
+ * context keeps a workspace, grown as needed; the context needs no
+ * sdp_setup).  Errors: SDP_E_INVALID (sizes, leading dimensions),
+ * SDP_E_NOMEM, SDP_E_CUDA, SDP_E_TIMEOUT (a bounded device wait gave up). */
+int sdp_dense_product(sdp_ctx* ctx, int trans_a, int trans_b, int M, int N, int K, double alpha, const double* A,
+                      int lda, const double* B, int ldb, double beta, double* C, int ldc);
+
 /* Solve `count` set-up contexts together: every ADMM step of all of them is
  * issued as one batched launch sequence (one launch per kernel for the
  * whole group, each CTA finding its instance through a prefix map); the

@@ -71,6 +71,7 @@ def lib():
         L.orc_rayleigh_ritz.argtypes = [C.c_int, _dp, C.c_int, _dp, _dp, _dp]
         L.orc_lobpcg.argtypes = [C.c_int, _dp, _ip, C.c_int, _dp, _dp, C.c_double, C.c_int, C.c_int,
                                  C.c_uint64, C.c_uint32, _ip, _dp]
+        L.orc_lobpcg_project.argtypes = [C.c_int, _dp, _ip, C.c_int, _dp, C.c_double, C.c_int, _dp, _ip]
         L.orc_admm_solve.argtypes = [C.c_int, _dp, C.POINTER(_Cons), _dp, C.POINTER(_Settings),
                                      _dp, _dp, _dp, _dp, _dp, C.POINTER(_Info)]
         _lib = L
@@ -226,6 +227,25 @@ def lobpcg(A, X0, tol, maxit=20, bexp=None, mcap=None, seed=0, stream=0):
     m = mm.value
     return {"rc": rc, "X": np.array(X[:, :m]), "lam": lam[:m].copy(), "resn": resn[:m].copy(), "m": m,
             "rr_steps": info[0], "expansions": info[1], "converged": bool(info[2]), "npos": info[3]}
+
+
+def lobpcg_project(A, X0, tol, maxit=20, mcap=None):
+    """Pi_{S+}(A) by LOBPCG (Algorithm 3) from the warm block X0 and the
+    reconstruction of Eq. 2, all in the C oracle (one thread).  Returns
+    (P, info dict)."""
+    A = _f64(A)
+    n = A.shape[0]
+    m = X0.shape[1]
+    if mcap is None:
+        mcap = n
+    X = np.zeros((n, mcap), order="F")
+    X[:, :m] = X0
+    out = np.zeros((n, n), order="F")
+    info = (C.c_int * 4)()
+    mm = C.c_int(m)
+    rc = lib().orc_lobpcg_project(n, _ptr(A), C.byref(mm), mcap, _ptr(X), tol, maxit, _ptr(out), info)
+    return out, {"rc": rc, "m": mm.value, "rr_steps": info[0], "expansions": info[1], "converged": bool(info[2]),
+                 "npos": info[3]}
 
 
 def default_settings(**kw):

@@ -697,6 +697,32 @@ done:
   return status;
 }
 
+/* Standalone projection by LOBPCG (Algorithm 3 for the positive
+ * eigenpairs from the warm block X, n x *m_io of an n x mcap buffer) and
+ * the reconstruction Pi(A) = sum over positive Ritz values theta x x^T
+ * (Eq. 2, first form).  out: n x n.  Returns the LOBPCG status. */
+int orc_lobpcg_project(int n, const double* A, int* m_io, int mcap, double* X, double tol, int maxit, double* out,
+                       int* info) {
+  double* lam = dalloc(mcap);
+  double* resn = dalloc(mcap);
+  int bexp = (int)ceil(n / 50.0);
+  if (bexp < 1) bexp = 1;
+  int rc = orc_lobpcg(n, A, m_io, mcap, X, lam, tol, maxit, bexp, 0, 0, info, resn);
+  for (size_t t = 0; t < (size_t)n * n; ++t) out[t] = 0.0;
+  if (rc == ORC_OK) {
+    for (int k = 0; k < *m_io; ++k) {
+      if (!(lam[k] > 0.0)) continue;
+      for (int j = 0; j < n; ++j) {
+        double vj = lam[k] * X[IDX(j, k, n)];
+        for (int i = 0; i < n; ++i) out[IDX(i, j, n)] += X[IDX(i, k, n)] * vj;
+      }
+    }
+  }
+  free(lam);
+  free(resn);
+  return rc;
+}
+
 /* ------------------------------------------------------------------ */
 /* Algorithm 1 on min <C,X> s.t. A(X) = b, X psd.                      */
 /* ------------------------------------------------------------------ */

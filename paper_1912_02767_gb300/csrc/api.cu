@@ -260,14 +260,38 @@ struct sdp_ctx {
   void* group_cache = nullptr;  // reusable engine state of a projection context
   double proj_res_pos2 = 0.0;
   int proj_steps = 0;
+  void* oz = nullptr;      // workspace of sdp_dense_product (grown on demand)
+  size_t oz_bytes = 0;
+  int* oz_err = nullptr;   // its wait-error flag
 };
 
 static void ctx_free(sdp_ctx* c) {
   if (c->dmem) cudaFree(c->dmem);
   if (c->dK) cudaFree(c->dK);
+  if (c->oz) cudaFree(c->oz);
+  if (c->oz_err) cudaFree(c->oz_err);
   c->dmem = nullptr;
   c->dK = nullptr;
+  c->oz = nullptr;
+  c->oz_err = nullptr;
+  c->oz_bytes = 0;
   c->ready = false;
+}
+
+// grow a device workspace to at least `need` bytes (contents not kept)
+static int grow_work(void** p, size_t* cap, size_t need) {
+  if (*cap >= need && *p) return SDP_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  const size_t want = need + need / 8;
+  if (cudaMalloc(p, want) != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return SDP_E_NOMEM;
+  }
+  *cap = want;
+  return SDP_OK;
 }
 
 extern "C" int sdp_create(sdp_ctx** out, const sdp_settings* settings, void* stream) {

@@ -137,7 +137,8 @@ struct Inst {
   Check* chk;
   double* chk_part;     // per-CTA partials of the check
   int prec;             // sdp_precision
-  int gram32;           // 1: the Grams S^T S, S^T A S are formed in FP32 (rr_fp32), else FP64
+  int piv_loose;        // 1: Cholesky-QR pivots below 1e-6 count as breakdown (the trial subspace's
+                        // products, hence S^T A S, carry split-BF16 or FP32 errors), else 1e-12
 };
 
 // State of a grid-wide barrier and of the cooperative kernels using it.

@@ -123,4 +123,14 @@ int tc_wprod(cudaStream_t s, const void* whi, const void* wlo, int ldw, const vo
              unsigned long long limit_ns);
 void split_bf16(cudaStream_t s, const double* src, int lds, int rows, int cols, void* hi, void* lo, int ldd);
 
+// oz_gemm.cu: C = alpha op(A) op(B) + beta C (FP64 column-major; op 'N' or
+// 'T') to FP64 accuracy on the tensor cores; `work` holds oz_work_bytes.
+// Returns 0, -1 (tensor maps / attributes refused, nothing launched) or -2
+// (work too small).  *err as for tc_wprod.
+size_t oz_work_bytes(int M, int N, int K);
+void symmetrize(cudaStream_t s, double* X, int p, int ld);
+int oz_gemm(cudaStream_t s, char ta, const double* A, int lda, char tb, const double* B, int ldb, int M, int N,
+            int K, double alpha, double beta, double* C, int ldc, void* work, size_t work_bytes, int* err,
+            int num_sms, unsigned long long limit_ns);
+
 }  // namespace sdpg

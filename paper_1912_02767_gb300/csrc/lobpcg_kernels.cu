@@ -508,7 +508,7 @@ __global__ void __launch_bounds__(1024) k_rr_smem(Inst* insts, const int* list, 
   for (int j = 0; j < p; ++j) {
     if (tid == 0) {
       T d = A[j + j * p];
-      if (!(d > (T)(I.gram32 ? 1e-6 : RRConst<T>::piv_min))) fail = j + 1;
+      if (!(d > (T)(I.piv_loose ? 1e-6 : RRConst<T>::piv_min))) fail = j + 1;
       A[j + j * p] = sqrt(d > (T)0 ? d : (T)1);
     }
     __syncthreads();

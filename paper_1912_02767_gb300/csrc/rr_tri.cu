@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(1024) k_rr_tri(Inst* insts, const int* list, i
 
   // breakdown threshold of Cholesky-QR: set by the precision the Gram was
   // formed in (FP32 Grams in the mixed modes), not by this kernel's type
-  const T piv = I.gram32 ? (T)1e-6 : (T)1e-12;  // the Gram's precision sets the breakdown threshold
+  const T piv = I.piv_loose ? (T)1e-6 : (T)1e-12;  // the products' precision sets the breakdown threshold
   // ---- 1. G = L~ D L~^T (right-looking, lower triangle of B)
   for (int t = tid; t < p * p; t += nt) {
     const int i = t % p, j = t / p;

@@ -97,6 +97,8 @@ def load():
     L.sdp_block_product.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int]
     L.sdp_project_psd_noalloc.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
     L.sdp_set_wait_limit.argtypes = [C.c_double]
+    L.sdp_dense_product.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_void_p,
+                                    C.c_int, C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_int]
     L.sdp_prof_enable.argtypes = [C.c_int]
     L.sdp_prof_enable.restype = None
     L.sdp_prof_reset.restype = None
@@ -155,6 +157,10 @@ def _check(rc, what):
 
 def _host_ptr(a, dtype):
     return a.ctypes.data_as(C.c_void_p)
+
+
+def _vp(t):
+    return C.c_void_p(t.data_ptr())
 
 
 def _stream_handle(stream):
@@ -251,6 +257,20 @@ class Context:
         k = B.shape[0]
         _check(self.lib.sdp_block_product(self.h, n, C.c_void_p(W.data_ptr()), C.c_void_p(B.data_ptr()), k,
                                           C.c_void_p(out.data_ptr()), 1 if resplit_w else 0), "sdp_block_product")
+
+    def dense_product(self, A, B, C, trans_a=False, trans_b=False, alpha=1.0, beta=0.0):
+        """sdp_dense_product on torch CUDA float64 tensors holding column-major
+        matrices: a column-major R x Q matrix is a contiguous torch tensor of
+        shape (Q, R).  C = alpha op(A) op(B) + beta C, FP64-accurate on the
+        tensor cores."""
+        Ar, Ac = A.shape[1], A.shape[0]
+        Br, Bc = B.shape[1], B.shape[0]
+        M, K = (Ac, Ar) if trans_a else (Ar, Ac)
+        Kb, N = (Bc, Br) if trans_b else (Br, Bc)
+        assert K == Kb and C.shape[1] == M and C.shape[0] == N
+        _check(self.lib.sdp_dense_product(self.h, 1 if trans_a else 0, 1 if trans_b else 0, M, N, K, float(alpha),
+                                          _vp(A), max(1, Ar), _vp(B),
+                                          max(1, Br), float(beta), _vp(C), max(1, M)), "sdp_dense_product")
 
     def project_raw(self, n, W_ptr, out_ptr, V_ptr, m, mcap, tol, on_device):
         """sdp_project_psd on raw pointers (column-major n x n W and out,

@@ -170,7 +170,8 @@ def test_theta_complete_graph_negative_mode(sdp, orc, prec):
     assert res["status_name"] == ref["status_name"] == "SOLVED"
     assert res["n_neg"] > res["n_lobpcg"] // 2 and res["n_neg"] > 100, res
     assert abs(res["obj"] - ref["obj"]) <= OBJ_TOL * abs(ref["obj"])
-    assert -res["obj"] == pytest.approx(1.0, abs=1e-5)
+    # closed form: FP64 to the stop rule's slack; mixed to the split-BF16 product level
+    assert -res["obj"] == pytest.approx(1.0, abs=1e-5 if prec == "fp64" else OBJ_TOL)
 
 
 def test_maxcut64_mixed_matches_oracle(sdp, orc):

@@ -115,3 +115,17 @@ def test_negative_mode_reconstruction_is_the_projection(orc):
     assert np.linalg.eigvalsh(Z).min() >= -1e-9 and np.linalg.eigvalsh(-Pneg).max() <= 1e-9
     planted = -W + Pneg                                                 # sign slip in the reconstruction
     assert np.linalg.norm(planted - exact) > 1e-2 * nW
+
+
+@pytest.mark.parametrize("n,f", [(80, 0.05), (120, 0.25)])
+def test_lobpcg_projection_matches_closed_form(orc, n, f):
+    """The oracle's standalone LOBPCG projection (Algorithm 3 + Eq. 2) from a
+    warm start perturbed by 1e-3 equals Q Lambda_+ Q^T; a reconstruction that
+    kept the negative Ritz values too would return W itself instead."""
+    sp = gen.random_spectrum(n, f, np.random.default_rng(900 + n))
+    nW = np.linalg.norm(sp["W"])
+    P, info = orc.lobpcg_project(sp["W"], sp["X0"], tol=1e-10)
+    assert info["rc"] == 0 and info["converged"] and info["npos"] == sp["k"]
+    exact = (sp["Q"] * np.maximum(sp["lam"], 0)) @ sp["Q"].T
+    assert np.linalg.norm(P - exact) <= 1e-8 * nW
+    assert np.linalg.norm(sp["W"] - exact) > 0.1 * nW
