@@ -57,10 +57,13 @@ typedef enum {
  * infeasibility tests are FP64 in every mode. */
 typedef enum {
   SDP_PREC_FP64 = 0,    /* every product, Gram and Rayleigh-Ritz in FP64 (CUDA cores)          */
-  SDP_PREC_BF16X3 = 1,  /* W*S on tcgen05 tensor cores with split-BF16 x3, FP32 accumulate; block     */
-                        /* update and reconstruction in FP32; Rayleigh-Ritz with its Grams and       */
-                        /* Cholesky-QR in FP64 (FP32 by the rr_fp32 setting); residual norms, ADMM   */
-                        /* state and tests FP64                                                      */
+  SDP_PREC_BF16X3 = 1,  /* W*S on tcgen05 tensor cores with split-BF16 x3, FP32 accumulate, raised to  */
+                        /* the FP64-accurate split product (see sdp_dense_product) for a projection    */
+                        /* whose tolerance or smallest |Ritz value| nears the x3 product's error       */
+                        /* (precision ladder); block update and reconstruction in FP32 (the update     */
+                        /* FP64-accurate on the tensor cores for wide blocks); Rayleigh-Ritz with its  */
+                        /* Grams and Cholesky-QR FP64-accurate (FP32 by the rr_fp32 setting);          */
+                        /* residual norms, ADMM state and tests FP64                                   */
   SDP_PREC_AUTO = 2     /* accepted; computes as SDP_PREC_BF16X3 (no tolerance-driven switch yet) */
 } sdp_precision;
 
@@ -110,6 +113,8 @@ typedef struct {
   int rank;            /* positive Ritz values at the last projection      */
   double solve_ms;     /* wall time of the solve (host clock)              */
   int n_neg;           /* LOBPCG projections done in negative mode         */
+  int n_ladder;        /* mixed precision: LOBPCG projections whose block  */
+                       /* products ran FP64-accurate (precision ladder)     */
 } sdp_info;
 
 typedef struct {
@@ -124,6 +129,8 @@ typedef struct {
   int jacobi_sweeps;   /* Jacobi sweeps summed over the Rayleigh-Ritz steps  */
   int mode;            /* 0 positive, 1 negative mode; 2 the exact fallback  */
                        /* (Cholesky-QR breakdown or block capacity)           */
+  int fp64_products;   /* mixed precision: 1 if the block products ran       */
+                       /* FP64-accurate (precision ladder), 0 split-BF16 x3   */
 } sdp_proj_info;
 
 /* Fill *s with the defaults listed above. */

@@ -260,6 +260,9 @@ struct sdp_ctx {
   void* group_cache = nullptr;  // reusable engine state of a projection context
   double proj_res_pos2 = 0.0;
   int proj_steps = 0;
+  // precision ladder (mixed precision): ||W||_F^2 and the smallest |Ritz
+  // value| seen by the last projection (0: unknown)
+  double wfro2 = 0.0, thmin = 0.0;
   void* oz = nullptr;      // workspace of sdp_dense_product (grown on demand)
   size_t oz_bytes = 0;
   int* oz_err = nullptr;   // its wait-error flag

@@ -71,6 +71,8 @@ struct Ctl {
   double res_max;  // largest Ritz residual norm of the block
   double res_pos2; // sum of squared residual norms of the positive pairs
   double jac_off;  // off-diagonal norm^2 (exact branch)
+  double wfro2;    // ||W||_F^2 of the matrix being projected (mixed precision)
+  double thmin;    // smallest |Ritz value| of the block (mixed precision)
 };
 
 // Per-instance reduction results of the termination check (Section 5).

@@ -53,8 +53,8 @@ __global__ void k_fro2_mat(const double* A, int ld, int rows, int cols, double* 
   if (threadIdx.x == 0) *dst = v;
 }
 
-// ||W||_F^2 into ctl->jac_off (ctl->jac_off zeroed by the host)
-__global__ void k_fro2(Inst* insts, WorkMap wm) {
+// ||W||_F^2 into ctl->jac_off (to_w = 0) or ctl->wfro2 (to_w = 1)
+__global__ void k_fro2(Inst* insts, WorkMap wm, int to_w) {
   __shared__ double sh[32];
   int local;
   const int ii = find_inst(wm, blockIdx.x, &local);
@@ -73,7 +73,7 @@ __global__ void k_fro2(Inst* insts, WorkMap wm) {
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
-    atomicAdd(&I.ctl->jac_off, s);
+    atomicAdd(to_w ? &I.ctl->wfro2 : &I.ctl->jac_off, s);
   }
 }
 

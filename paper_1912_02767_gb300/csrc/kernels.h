@@ -106,7 +106,7 @@ __global__ void k_jac_angles(Inst* insts, WorkMap wm, int round);
 __global__ void k_jac_apply(Inst* insts, WorkMap wm, int round);
 __global__ void k_jac_sort(Inst* insts, const int* list);
 __global__ void k_jac_gather(Inst* insts, WorkMap wm);
-__global__ void k_fro2(Inst* insts, WorkMap wm);
+__global__ void k_fro2(Inst* insts, WorkMap wm, int to_w);
 __global__ void k_fro2_det(Inst* insts, const int* list);
 __global__ void k_fro2_mat(const double* A, int ld, int rows, int cols, double* dst);
 __global__ void k_seed_block(Inst* insts, WorkMap wm);

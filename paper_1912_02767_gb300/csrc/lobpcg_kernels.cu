@@ -299,12 +299,13 @@ __global__ void k_resid_finish(Inst* insts, const int* list, int last_allowed) {
   Ctl* c = I.ctl;
   if (threadIdx.x != 0) return;
   const int m = c->m, mP = c->mP;
-  double rmax = 0.0, rpos2 = 0.0;
+  double rmax = 0.0, rpos2 = 0.0, thmin = 1e300;
   int npos = 0, ma = 0, mPa = 0;
   for (int j = 0; j < m; ++j) {
     double r = I.resn[j];
     bool fresh = j >= m - c->nfresh;
     rmax = fmax(rmax, r);
+    if (!fresh) thmin = fmin(thmin, fabs(I.theta[j]));
     if (!fresh && I.theta[j] > 0.0) {
       ++npos;
       rpos2 += r * r;
@@ -316,6 +317,7 @@ __global__ void k_resid_finish(Inst* insts, const int* list, int last_allowed) {
     if (I.slot[j] >= 0 && I.resn[m + j] > 0.0) ++mPa;
   c->res_max = rmax;
   c->res_pos2 = rpos2;
+  c->thmin = thmin;
   c->npos = npos;
   c->ma = ma;
   c->mPa = mPa;

@@ -34,7 +34,8 @@ class Settings(C.Structure):
 class Info(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("obj", C.c_double), ("r_prim", C.c_double),
                 ("r_dual", C.c_double), ("n_exact", C.c_int), ("n_lobpcg", C.c_int), ("lobpcg_steps", C.c_int),
-                ("expansions", C.c_int), ("rank", C.c_int), ("solve_ms", C.c_double), ("n_neg", C.c_int)]
+                ("expansions", C.c_int), ("rank", C.c_int), ("solve_ms", C.c_double), ("n_neg", C.c_int),
+                ("n_ladder", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -43,7 +44,7 @@ class Info(C.Structure):
 class ProjInfo(C.Structure):
     _fields_ = [("status", C.c_int), ("steps", C.c_int), ("m", C.c_int), ("npos", C.c_int),
                 ("expansions", C.c_int), ("converged", C.c_int), ("res_fro", C.c_double),
-                ("jacobi_sweeps", C.c_int), ("mode", C.c_int)]
+                ("jacobi_sweeps", C.c_int), ("mode", C.c_int), ("fp64_products", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
