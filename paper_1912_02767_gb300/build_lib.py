@@ -14,7 +14,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsdpgpu.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-rdc=false", "-static-global-template-stub=false"]
-SOURCES = ["api.cu", "host_setup.cu", "admm_kernels.cu", "lobpcg_kernels.cu", "jacobi_kernels.cu", "rr_large.cu", "tc_gemm.cu", "bj_eig.cu", "rr_tri.cu", "rr_wide.cu", "oz_gemm.cu"]
+SOURCES = ["api.cu", "host_setup.cu", "admm_kernels.cu", "lobpcg_kernels.cu", "jacobi_kernels.cu", "rr_large.cu", "tc_gemm.cu", "bj_eig.cu", "rr_tri.cu", "rr_wide.cu", "oz_gemm.cu", "rr_blocked.cu"]
 
 
 def nvcc():

@@ -100,6 +100,15 @@ constexpr int kTridBacktrNv = 16;  // vectors per CTA of k_trid_backtr (at most)
 inline size_t rr_backtr_smem_bytes(int p, int nv, int tsize) { return (size_t)(nv + 4) * p * tsize; }
 constexpr size_t kBacktrSmemMax = 230400;  // 227 KiB per CTA less the kernel's static shared memory (<= 2 KiB)
 
+// rr_blocked.cu (blocked Cholesky/inverse and compact-WY back-transform,
+// their products on the tensor cores)
+constexpr int kBlk = 128;  // diagonal block / reflector block width
+constexpr size_t kBlkSmem = (size_t)kBlk * (kBlk + 1) * sizeof(double);
+__global__ void k_potrf_inv_block(double* G, int ldg, double* Linv, int ldl, int j0, int bb, double piv_min,
+                                  GridBar* bar);
+__global__ void k_wy_vmat(const double* A, int p, int nref, double* V);
+__global__ void k_wy_tmat(double* Tall, const double* tau, int nref);
+
 // jacobi_kernels.cu (exact branch)
 __global__ void k_jac_init(Inst* insts, WorkMap wm, int negate);
 __global__ void k_jac_angles(Inst* insts, WorkMap wm, int round);
