@@ -86,6 +86,14 @@ __global__ void k_rr_large_finish(Ctl* ctl, const GridBar* b);
 // rr_wide.cu (one wide subspace over the whole GPU, tridiagonal route)
 template <typename T>
 __global__ void k_trid_coop(const double* H, T* A, int p, int keep, double* vb, GridBar* b);
+template <typename T>
+__global__ void k_trid_tail(const T* A, int p, int keep, double* vb, GridBar* b);
+constexpr int kLatrdNb = 64;   // panel width of the blocked tridiagonalization
+constexpr int kLatrdOwn = 64;  // owned columns per CTA it can hold (grid >= p / 63)
+__global__ void k_latrd_coop(double* A, int p, int keep, int j0, int j1, double* Vp, double* Wp, double* Kg,
+                             double* pt, double* vb, GridBar* b);
+__global__ void k_latrd_wfinal(const double* Vp, double* Wp, const double* Kg, int p, int r0, int nc);
+__global__ void k_sym_copy(const double* H, double* A, int p);
 template <typename TS, typename T>
 __global__ void k_trid_eig(double* vb, int p, int keep, int S, int refine, int final, double* theta, int* npos,
                            const GridBar* b);

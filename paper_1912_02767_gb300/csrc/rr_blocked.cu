@@ -18,19 +18,26 @@
 
 namespace sdpg {
 
+__device__ __forceinline__ double warp_sum_d(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 // One CTA: the bb x bb diagonal block of G at (j0, j0) (bb <= kBlk): its
 // Cholesky factor L11 (lower, written back into G with zeros above) and
 // L11^{-1} (written into Linv's diagonal block).  A pivot d <= piv_min (the
 // Schur complement's diagonal before the square root) records the 1-based
-// column in bar->fail; the block is then left as it is.
+// column in bar->fail; the block is then left as it is.  The inverse is
+// formed by forward substitution, one column per warp (lanes split each dot
+// product), into the upper triangle of the shared block (transposed).
 // Dynamic shared memory: kBlkSmem bytes.
 __global__ void __launch_bounds__(1024) k_potrf_inv_block(double* G, int ldg, double* Linv, int ldl, int j0, int bb,
                                                           double piv_min, GridBar* bar) {
   extern __shared__ __align__(16) unsigned char smraw[];
   double (*A)[kBlk + 1] = (double (*)[kBlk + 1])smraw;
-  __shared__ double x[kBlk];
+  __shared__ double xd[kBlk];
   __shared__ int fail;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   if (*(volatile int*)&bar->fail || *(volatile int*)&bar->err) return;
   for (int t = tid; t < bb * bb; t += nt) {
     const int i = t % bb, j = t / bb;
@@ -45,15 +52,14 @@ __global__ void __launch_bounds__(1024) k_potrf_inv_block(double* G, int ldg, do
       if (tid == 0) fail = j0 + j + 1;
       break;  // uniform: every thread read the same pivot
     }
-    const double s = sqrt(d), inv = 1.0 / s;
+    const double sq = sqrt(d), inv = 1.0 / sq;
     __syncthreads();
-    if (tid == 0) A[j][j] = s;
+    if (tid == 0) A[j][j] = sq;
     for (int r = j + 1 + tid; r < bb; r += nt) A[r][j] *= inv;
     __syncthreads();
-    const int w = bb - j - 1;
-    for (int t = tid; t < w * w; t += nt) {
-      const int r = j + 1 + t % w, c = j + 1 + t / w;
-      if (c <= r) A[r][c] -= A[r][j] * A[c][j];
+    for (int c = j + 1 + wid; c < bb; c += nw) {
+      const double lc = A[c][j];
+      for (int r = c + lane; r < bb; r += 32) A[r][c] -= A[r][j] * lc;
     }
     __syncthreads();
   }
@@ -66,24 +72,22 @@ __global__ void __launch_bounds__(1024) k_potrf_inv_block(double* G, int ldg, do
     const int i = t % bb, j = t / bb;
     G[(size_t)(j0 + i) + (size_t)(j0 + j) * ldg] = i >= j ? A[i][j] : 0.0;
   }
+  for (int j = tid; j < bb; j += nt) xd[j] = 1.0 / A[j][j];
   __syncthreads();
-  // in-place inverse of the lower-triangular block, last column first:
-  // column j of L^{-1} = -(L^{-1})_{j+1:, j+1:} L_{j+1:, j} / L_jj below 1/L_jj
-  for (int j = bb - 1; j >= 0; --j) {
-    const double ajj = 1.0 / A[j][j];
-    for (int r = j + 1 + tid; r < bb; r += nt) x[r] = A[r][j];
-    __syncthreads();
-    for (int r = j + 1 + tid; r < bb; r += nt) {
-      double acc = 0.0;
-      for (int c = j + 1; c <= r; ++c) acc += A[r][c] * x[c];
-      A[r][j] = -acc * ajj;
+  // X = L^{-1}: column j solves L x = e_j; X[i][j] kept at A[j][i] (i > j)
+  for (int j = wid; j < bb; j += nw) {
+    for (int i = j + 1; i < bb; ++i) {
+      double acc = lane == 0 ? A[i][j] * xd[j] : 0.0;  // k = j term: L_ij X_jj
+      for (int k = j + 1 + lane; k < i; k += 32) acc += A[i][k] * A[j][k];
+      acc = warp_sum_d(acc);
+      if (lane == 0) A[j][i] = -acc * xd[i];
+      __syncwarp();
     }
-    if (tid == 0) A[j][j] = ajj;
-    __syncthreads();
   }
+  __syncthreads();
   for (int t = tid; t < bb * bb; t += nt) {
     const int i = t % bb, j = t / bb;
-    Linv[(size_t)(j0 + i) + (size_t)(j0 + j) * ldl] = i >= j ? A[i][j] : 0.0;
+    Linv[(size_t)(j0 + i) + (size_t)(j0 + j) * ldl] = i > j ? A[j][i] : (i == j ? xd[i] : 0.0);
   }
 }
 

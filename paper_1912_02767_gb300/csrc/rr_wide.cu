@@ -59,6 +59,73 @@ __device__ __forceinline__ T block_sum(T v, T* red) {
   return warp_sum(s);
 }
 
+// Tail of the reduction (one CTA): the last 2 x 2 block into (d, e), the
+// Gershgorin scaling of (d, e) to unit norm, e^2; non-finite data marks a
+// breakdown.  (d, e) may come from other CTAs: read past L1.
+template <typename T>
+__device__ void trid_tail(const T* A, int p, WideVec<T>& V, GridBar* b) {
+  __shared__ T rlo[32], rhi[32];
+  __shared__ T tscal;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  if (tid == 0) {
+    if (p >= 2) {
+      V.d[p - 2] = __ldcg(A + (size_t)(p - 2) * p + (p - 2));
+      V.d[p - 1] = __ldcg(A + (size_t)(p - 1) * p + (p - 1));
+      V.e[p - 2] = __ldcg(A + (size_t)(p - 2) * p + (p - 1));
+    } else {
+      V.d[0] = __ldcg(A);
+    }
+  }
+  __syncthreads();
+  T lo = 0, hi = 0;
+  int bad = 0;
+  for (int i = tid; i < p; i += nt) {
+    const T di = __ldcg(V.d + i);
+    const T off = (i > 0 ? fabs(__ldcg(V.e + i - 1)) : (T)0) + (i + 1 < p ? fabs(__ldcg(V.e + i)) : (T)0);
+    lo = fmin(lo, di - off);
+    hi = fmax(hi, di + off);
+    bad |= !isfinite(di) || !isfinite(off);
+  }
+  lo = warp_min(lo);
+  hi = warp_max(hi);
+  bad = __syncthreads_or(bad);
+  if (lane == 0) {
+    rlo[wid] = lo;
+    rhi[wid] = hi;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    T l = 0, h = 0;
+    for (int w2 = 0; w2 < nw; ++w2) {
+      l = fmin(l, rlo[w2]);
+      h = fmax(h, rhi[w2]);
+    }
+    T nrm = fmax(fabs(l), fabs(h));
+    nrm = nrm > (T)0 ? nrm : (T)1;
+    V.sc[0] = (double)nrm;
+    V.sc[1] = 1.0 / (double)nrm;
+    tscal = (T)1 / nrm;
+    if (bad) atomicCAS(&b->fail, 0, -3);  // non-finite data: breakdown
+  }
+  __syncthreads();
+  const T itn = tscal;
+  for (int i = tid; i < p; i += nt) {
+    V.d[i] = __ldcg(V.d + i) * itn;
+    if (i + 1 < p) {
+      const T ei = __ldcg(V.e + i) * itn;
+      V.e[i] = ei;
+      V.e2[i] = ei * ei;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_trid_tail(const T* A, int p, int keep, double* vb, GridBar* b) {
+  WideVec<T> V(vb, p, keep);
+  if (bar_failed(b)) return;
+  trid_tail(A, p, V, b);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(1024) k_trid_coop(const double* H, T* A, int p, int keep, double* vb, GridBar* b) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -150,59 +217,171 @@ __global__ void __launch_bounds__(1024) k_trid_coop(const double* H, T* A, int p
     if (!gbar(b)) return;
   }
   if (bid != 0) return;
-  // tail (CTA 0): last 2 x 2 block, Gershgorin scaling, e^2
-  if (tid == 0) {
-    if (p >= 2) {
-      V.d[p - 2] = __ldcg(A + (size_t)(p - 2) * p + (p - 2));
-      V.d[p - 1] = __ldcg(A + (size_t)(p - 1) * p + (p - 1));
-      V.e[p - 2] = __ldcg(A + (size_t)(p - 2) * p + (p - 1));
-    } else {
-      V.d[0] = __ldcg(A);
+  trid_tail(A, p, V, b);  // CTA 0
+}
+
+// One panel [j0, j1) of the blocked Householder tridiagonalization of the
+// symmetric A (p x p, ld p, full storage), for the mixed path (its trailing
+// updates run on the tensor cores).  For every column k of the panel (c =
+// k - j0), with V, W the panel's earlier Householder vectors and their
+// w-vectors (W kept before the correction w -= K v, K per column in Kc):
+//   (a) column k below the diagonal minus the earlier rank-2 terms
+//       V W[k, :]^T + W V[k, :]^T, on this CTA's rows (i = bid mod G);
+//   (b) the reflector P = I - t v v^T of the updated column (every CTA,
+//       same data, fixed order), s = A22 v on the owned columns (A22 not yet
+//       updated by the panel: columns right of k are untouched here), and
+//       the partial sums of W^T v, V^T v over the owned rows;
+//   (c) w = t (s - V (W^T v) - W (V^T v)) on the owned entries, stored with
+//       v into the panels (v also below the subdiagonal of A for the
+//       back-transform); K = t/2 w^T v.
+// Three grid barriers per column; the host then applies A22 -= V W^T +
+// W V^T (W corrected by K) as two FP64-accurate products.  pt holds per CTA
+// [norm^2, w^T v, W^T v (kLatrdNb), V^T v (kLatrdNb)] partial sums.
+// Dynamic shared memory: (p + kLatrdOwn + 3 kLatrdNb) doubles.
+__global__ void __launch_bounds__(1024) k_latrd_coop(double* A, int p, int keep, int j0, int j1, double* Vp,
+                                                      double* Wp, double* Kg, double* pt, double* vb, GridBar* b) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double* vs = (double*)smraw;  // Householder vector of the step (v_0 = 1)
+  double* sj = vs + p;          // A22 v on the owned columns
+  double* y1 = sj + kLatrdOwn;  // W^T v
+  double* y2 = y1 + kLatrdNb;   // V^T v
+  double* Kc = y2 + kLatrdNb;   // K of the panel's columns
+  __shared__ double red[32];
+  __shared__ double scal[2];
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  const int G = gridDim.x, bid = blockIdx.x;
+  const int PT = 2 + 2 * kLatrdNb;
+  WideVec<double> V(vb, p, keep);
+  if (bar_failed(b)) return;
+  if (j1 - j0 > kLatrdNb || (p - j0 + G - 1) / G > kLatrdOwn) {  // launch sized for another width: refuse
+    if (bid == 0 && tid == 0) atomicCAS(&b->fail, 0, -4);
+    return;
+  }
+  for (int k = j0; k < j1; ++k) {
+    const int c = k - j0, r = p - k - 1;
+    // (a) owned rows i >= k of column k
+    const int ifirst = k + ((bid - k) % G + G) % G;
+    double pn = 0.0;
+    for (int i = ifirst + wid * G; i < p; i += nw * G) {
+      double acc = 0.0;
+      for (int q = lane; q < c; q += 32) {
+        const double vk = __ldcg(Vp + k + (size_t)q * p), wk = __ldcg(Wp + k + (size_t)q * p) - Kc[q] * vk;
+        const double vi = __ldcg(Vp + i + (size_t)q * p), wi = __ldcg(Wp + i + (size_t)q * p) - Kc[q] * vi;
+        acc += vi * wk + wi * vk;
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) {
+        const double x = __ldcg(A + i + (size_t)k * p) - acc;
+        A[i + (size_t)k * p] = x;
+        if (i >= k + 2) pn += x * x;
+      }
     }
-  }
-  __syncthreads();
-  // (d, e) were written by the owners of their columns: read past L1
-  T lo = 0, hi = 0;
-  int bad = 0;
-  for (int i = tid; i < p; i += nt) {
-    const T di = __ldcg(V.d + i);
-    const T off = (i > 0 ? fabs(__ldcg(V.e + i - 1)) : (T)0) + (i + 1 < p ? fabs(__ldcg(V.e + i)) : (T)0);
-    lo = fmin(lo, di - off);
-    hi = fmax(hi, di + off);
-    bad |= !isfinite(di) || !isfinite(off);
-  }
-  lo = warp_min(lo);
-  hi = warp_max(hi);
-  bad = __syncthreads_or(bad);
-  __shared__ T rlo[32], rhi[32];
-  if (lane == 0) {
-    rlo[wid] = lo;
-    rhi[wid] = hi;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    T l = 0, h = 0;
-    for (int w2 = 0; w2 < nw; ++w2) {
-      l = fmin(l, rlo[w2]);
-      h = fmax(h, rhi[w2]);
+    pn = block_sum(pn, red);
+    if (tid == 0) pt[(size_t)bid * PT] = pn;
+    if (!gbar(b)) return;
+    // (b) the reflector, from every CTA's partial norm in a fixed order
+    if (tid == 0) {
+      double sn = 0.0;
+      for (int g = 0; g < G; ++g) sn += __ldcg(pt + (size_t)g * PT);
+      const double x0 = __ldcg(A + (k + 1) + (size_t)k * p);
+      double beta = x0, t = 0.0, scale = 0.0;
+      if (sn > 0.0) {
+        const double alpha = sqrt(x0 * x0 + sn);
+        beta = x0 >= 0.0 ? -alpha : alpha;
+        t = (beta - x0) / beta;
+        scale = 1.0 / (x0 - beta);
+      }
+      scal[0] = t;
+      scal[1] = scale;
+      if (bid == 0) {
+        V.d[k] = __ldcg(A + k + (size_t)k * p);
+        V.e[k] = beta;
+        V.tau[k] = t;
+      }
     }
-    T nrm = fmax(fabs(l), fabs(h));
-    nrm = nrm > (T)0 ? nrm : (T)1;
-    V.sc[0] = (double)nrm;
-    V.sc[1] = 1.0 / (double)nrm;
-    scal[0] = (T)1 / nrm;
-    if (bad) atomicCAS(&b->fail, 0, -3);  // non-finite data: breakdown
-  }
-  __syncthreads();
-  const T itn = scal[0];
-  for (int i = tid; i < p; i += nt) {
-    V.d[i] = __ldcg(V.d + i) * itn;
-    if (i + 1 < p) {
-      const T ei = __ldcg(V.e + i) * itn;
-      V.e[i] = ei;
-      V.e2[i] = ei * ei;
+    __syncthreads();
+    const double t = scal[0], scale = scal[1];
+    for (int i = tid; i < r; i += nt) vs[i] = i == 0 ? 1.0 : __ldcg(A + (k + 1 + i) + (size_t)k * p) * scale;
+    __syncthreads();
+    const int jfirst = (k + 1) + ((bid - (k + 1)) % G + G) % G;
+    for (int j = jfirst + wid * G, oj = wid; j < p; j += nw * G, oj += nw) {
+      const double* col = A + (size_t)j * p + (k + 1);
+      double acc = 0.0;
+      for (int i = lane; i < r; i += 32) acc += col[i] * vs[i];
+      acc = warp_sum(acc);
+      if (lane == 0) sj[oj] = acc;
     }
+    for (int q = wid; q < c; q += nw) {
+      double a1 = 0.0, a2 = 0.0;
+      for (int i = jfirst + lane * G; i < p; i += 32 * G) {
+        const double vi = vs[i - k - 1];
+        const double vp = __ldcg(Vp + i + (size_t)q * p), wf = __ldcg(Wp + i + (size_t)q * p) - Kc[q] * vp;
+        a1 += wf * vi;
+        a2 += vp * vi;
+      }
+      a1 = warp_sum(a1);
+      a2 = warp_sum(a2);
+      if (lane == 0) {
+        pt[(size_t)bid * PT + 2 + q] = a1;
+        pt[(size_t)bid * PT + 2 + kLatrdNb + q] = a2;
+      }
+    }
+    if (!gbar(b)) return;
+    // (c) w on the owned entries
+    for (int q = tid; q < c; q += nt) {
+      double a1 = 0.0, a2 = 0.0;
+      for (int g = 0; g < G; ++g) {
+        a1 += __ldcg(pt + (size_t)g * PT + 2 + q);
+        a2 += __ldcg(pt + (size_t)g * PT + 2 + kLatrdNb + q);
+      }
+      y1[q] = a1;
+      y2[q] = a2;
+    }
+    __syncthreads();
+    double pw = 0.0;
+    for (int j = jfirst + wid * G, oj = wid; j < p; j += nw * G, oj += nw) {
+      double corr = 0.0;
+      for (int q = lane; q < c; q += 32) {
+        const double vp = __ldcg(Vp + j + (size_t)q * p), wf = __ldcg(Wp + j + (size_t)q * p) - Kc[q] * vp;
+        corr += vp * y1[q] + wf * y2[q];
+      }
+      corr = warp_sum(corr);
+      if (lane == 0) {
+        const double w = t * (sj[oj] - corr), vj = vs[j - k - 1];
+        Wp[j + (size_t)c * p] = w;
+        Vp[j + (size_t)c * p] = vj;
+        if (j >= k + 2) A[j + (size_t)k * p] = vj;  // Householder vector below the subdiagonal
+        pw += w * vj;
+      }
+    }
+    pw = block_sum(pw, red);
+    if (tid == 0) pt[(size_t)bid * PT + 1] = pw;
+    if (!gbar(b)) return;
+    if (tid == 0) {
+      double sw = 0.0;
+      for (int g = 0; g < G; ++g) sw += __ldcg(pt + (size_t)g * PT + 1);
+      Kc[c] = 0.5 * t * sw;
+      if (bid == 0) Kg[c] = Kc[c];
+    }
+    __syncthreads();
   }
+}
+
+// W[:, c] -= K_c V[:, c] for rows r0.. of the panel's nc columns
+__global__ void k_latrd_wfinal(const double* Vp, double* Wp, const double* Kg, int p, int r0, int nc) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int rows = p - r0;
+  if (t >= (long long)rows * nc) return;
+  const int i = r0 + (int)(t % rows), c = (int)(t / rows);
+  Wp[i + (size_t)c * p] -= Kg[c] * Vp[i + (size_t)c * p];
+}
+
+// A = (H + H^T) / 2 (p x p, ld p)
+__global__ void k_sym_copy(const double* H, double* A, int p) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)p * p) return;
+  const int i = (int)(t % p), j = (int)(t / p);
+  A[t] = 0.5 * (H[t] + H[(size_t)i * p + j]);
 }
 
 // Top `keep` eigenvalues of the scaled tridiagonal.  TS is the precision of
@@ -350,6 +529,7 @@ __global__ void __launch_bounds__(256) k_trid_backtr(const T* A, double* vb, int
 
 template __global__ void k_trid_coop<float>(const double*, float*, int, int, double*, GridBar*);
 template __global__ void k_trid_coop<double>(const double*, double*, int, int, double*, GridBar*);
+template __global__ void k_trid_tail<double>(const double*, int, int, double*, GridBar*);
 template __global__ void k_trid_eig<float, float>(double*, int, int, int, int, int, double*, int*, const GridBar*);
 template __global__ void k_trid_eig<float, double>(double*, int, int, int, int, int, double*, int*, const GridBar*);
 template __global__ void k_trid_eig<double, double>(double*, int, int, int, int, int, double*, int*, const GridBar*);
