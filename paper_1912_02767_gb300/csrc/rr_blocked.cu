@@ -46,15 +46,23 @@ __global__ void __launch_bounds__(1024) k_potrf_inv_block(double* G, int ldg, do
   if (tid == 0) fail = 0;
   __syncthreads();
   // right-looking Cholesky of the block
+  // (the pivot's square root and reciprocal by one thread: an SM issues only
+  // about two FP64 operations per clock, so redundant FP64 work is costly)
+  __shared__ double s_inv;
   for (int j = 0; j < bb; ++j) {
     const double d = A[j][j];
     if (!(d > piv_min)) {
       if (tid == 0) fail = j0 + j + 1;
       break;  // uniform: every thread read the same pivot
     }
-    const double sq = sqrt(d), inv = 1.0 / sq;
     __syncthreads();
-    if (tid == 0) A[j][j] = sq;
+    if (tid == 0) {
+      const double sq = sqrt(d);
+      A[j][j] = sq;
+      s_inv = 1.0 / sq;
+    }
+    __syncthreads();
+    const double inv = s_inv;
     for (int r = j + 1 + tid; r < bb; r += nt) A[r][j] *= inv;
     __syncthreads();
     for (int c = j + 1 + wid; c < bb; c += nw) {

@@ -79,16 +79,22 @@ __global__ void __launch_bounds__(1024) k_rr_tri(Inst* insts, const int* list, i
       if (tid == 0) s_fail = j + 1;
       break;  // every thread reads the same pivot: uniform exit
     }
-    // scalar work only in the warps that use it (FP64 issue is scarce)
+    // scalar work only in the warps that use it, one lane each (an SM
+    // issues about two FP64 operations per clock: a division in every
+    // thread of the block would cost more than the update itself)
     if (j + 1 + wid < p) {
-      const T inv = (T)1 / djj;
+      T inv = (T)0;
+      if (lane == 0) inv = (T)1 / djj;
+      inv = __shfl_sync(0xffffffffu, inv, 0);
       for (int c = j + 1 + wid; c < p; c += nw) {
         const T bc = B[c + j * ldp] * inv;
         for (int r = c + lane; r < p; r += 32) B[r + c * ldp] -= B[r + j * ldp] * bc;
       }
     }
-    if (j > 0 && j + tid < p) {  // column j-1 is no longer read: scale it to L~
-      const T invp = (T)1 / B[(j - 1) + (j - 1) * ldp];
+    if (j > 0 && j + (tid & ~31) < p) {  // column j-1 is no longer read: scale it to L~
+      T invp = (T)0;
+      if (lane == 0) invp = (T)1 / B[(j - 1) + (j - 1) * ldp];
+      invp = __shfl_sync(0xffffffffu, invp, 0);
       for (int r = j + tid; r < p; r += nt) B[r + (j - 1) * ldp] *= invp;
     }
     __syncthreads();
@@ -153,12 +159,15 @@ __global__ void __launch_bounds__(1024) k_rr_tri(Inst* insts, const int* list, i
       s = warp_sum(s);
       const T x0 = colk[0];
       T beta = x0, t = 0, scale = 0;
-      if (s > (T)0) {  // P = I - t v v^T with v_0 = 1 maps x to beta e_1
+      if (lane == 0 && s > (T)0) {  // P = I - t v v^T with v_0 = 1 maps x to beta e_1
         const T alpha = sqrt(x0 * x0 + s);
         beta = x0 >= (T)0 ? -alpha : alpha;
         t = (beta - x0) / beta;
         scale = (T)1 / (x0 - beta);
       }
+      beta = __shfl_sync(0xffffffffu, beta, 0);
+      t = __shfl_sync(0xffffffffu, t, 0);
+      scale = __shfl_sync(0xffffffffu, scale, 0);
       for (int i = lane; i < r; i += 32) {
         const T v = i == 0 ? (T)1 : colk[i] * scale;
         vv[i] = v;
@@ -335,7 +344,9 @@ __global__ void __launch_bounds__(1024) k_rr_tri(Inst* insts, const int* list, i
     if (wid * 32 < p) {
       T nrm2 = lane * 32 < p ? s_red[lane] : (T)0;
       nrm2 = warp_sum(nrm2);
-      const T sc = nrm2 > (T)0 ? (T)1 / sqrt(nrm2) : (T)1;
+      T sc = (T)1;
+      if (lane == 0 && nrm2 > (T)0) sc = (T)1 / sqrt(nrm2);  // one lane per warp (FP64 issue is scarce)
+      sc = __shfl_sync(0xffffffffu, sc, 0);
       for (int i = tid; i < p; i += nt) Z[(size_t)i * keep + q] *= sc;
     }
     __syncthreads();

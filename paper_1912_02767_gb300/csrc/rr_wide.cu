@@ -279,10 +279,16 @@ __global__ void __launch_bounds__(1024) k_latrd_coop(double* A, int p, int keep,
     pn = block_sum(pn, red);
     if (tid == 0) pt[(size_t)bid * PT] = pn;
     if (!gbar(b)) return;
-    // (b) the reflector, from every CTA's partial norm in a fixed order
-    if (tid == 0) {
+    // (b) the reflector, from every CTA's partial norm (one warp, fixed order)
+    if (wid == 0) {
       double sn = 0.0;
-      for (int g = 0; g < G; ++g) sn += __ldcg(pt + (size_t)g * PT);
+      for (int g = lane; g < G; g += 32) sn += __ldcg(pt + (size_t)g * PT);
+      sn = warp_sum(sn);
+      if (lane == 0) red[0] = sn;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const double sn = red[0];
       const double x0 = __ldcg(A + (k + 1) + (size_t)k * p);
       double beta = x0, t = 0.0, scale = 0.0;
       if (sn > 0.0) {
@@ -328,14 +334,18 @@ __global__ void __launch_bounds__(1024) k_latrd_coop(double* A, int p, int keep,
     }
     if (!gbar(b)) return;
     // (c) w on the owned entries
-    for (int q = tid; q < c; q += nt) {
+    for (int q = wid; q < c; q += nw) {  // a warp per q, lanes over the CTAs
       double a1 = 0.0, a2 = 0.0;
-      for (int g = 0; g < G; ++g) {
+      for (int g = lane; g < G; g += 32) {
         a1 += __ldcg(pt + (size_t)g * PT + 2 + q);
         a2 += __ldcg(pt + (size_t)g * PT + 2 + kLatrdNb + q);
       }
-      y1[q] = a1;
-      y2[q] = a2;
+      a1 = warp_sum(a1);
+      a2 = warp_sum(a2);
+      if (lane == 0) {
+        y1[q] = a1;
+        y2[q] = a2;
+      }
     }
     __syncthreads();
     double pw = 0.0;
@@ -357,11 +367,14 @@ __global__ void __launch_bounds__(1024) k_latrd_coop(double* A, int p, int keep,
     pw = block_sum(pw, red);
     if (tid == 0) pt[(size_t)bid * PT + 1] = pw;
     if (!gbar(b)) return;
-    if (tid == 0) {
+    if (wid == 0) {
       double sw = 0.0;
-      for (int g = 0; g < G; ++g) sw += __ldcg(pt + (size_t)g * PT + 1);
-      Kc[c] = 0.5 * t * sw;
-      if (bid == 0) Kg[c] = Kc[c];
+      for (int g = lane; g < G; g += 32) sw += __ldcg(pt + (size_t)g * PT + 1);
+      sw = warp_sum(sw);
+      if (lane == 0) {
+        Kc[c] = 0.5 * t * sw;
+        if (bid == 0) Kg[c] = Kc[c];
+      }
     }
     __syncthreads();
   }
