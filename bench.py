@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--sizes", default="256,1024,4096")
     ap.add_argument("--fracs", default="0.01,0.05,0.25")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-admm", action="store_true", help="skip the max-cut n=64 ADMM solves beside the sweep")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="sweep", choices=["sweep", "maxcut64", "theta500", "batch", "serve"],
                     help="sweep: the projection sweep (the bench line); the others time ADMM solves")
@@ -156,6 +157,48 @@ def run_dense(args):
             "bf16_peak_tflops": pk.get("bf16_tflops"), "max_rel_err_vs_cublas_fp64": err, "calls": len(evs),
             "note": "each call also slices both operands (two row-scale and two slicing kernels)"}
     print(json.dumps(line), flush=True)
+
+
+def kernel_rooflines(named, pk, total_ms):
+    """Per named kernel (launch group), largest time first: the achieved rate
+    of its algorithmic work against the peak of the unit bounding it.
+      k_tc_wprod               HBM bytes / measured copy bandwidth
+      oz_gemm                  FP64-equivalent flops against the split
+                               product's FP64-equivalent peak, the measured
+                               sustained bf16 peak / 21 (21 bf16 digit products
+                               per FP64 product), and executed bf16 flops
+                               against the bf16 peak
+      everything else          FP64 flops (CUDA cores) against the nominal
+      (FP64 CUDA-core kernels) GB300 FP64 peak (no measured FP64 figure)"""
+    bf16 = pk.get("bf16_tflops_sustained") or pk.get("bf16_tflops") or 1700.0
+    hbm = pk.get("hbm_gbs", 6800.0)
+    out = []
+    for name, v in sorted(named.items(), key=lambda kv: -kv[1]["ms"]):
+        if v["ms"] <= 0 or v["timed"] == 0:
+            continue
+        t = v["ms"] / 1000.0
+        r = {"kernel": name, "launches": v["timed"], "ms": round(v["ms"], 3),
+             "avg_launch_ms": v["ms"] / v["timed"], "share_of_step": round(v["ms"] / max(total_ms, 1e-9), 4),
+             "traffic": None}
+        if name == "k_tc_wprod":
+            a = v["bytes"] / t / 1e9
+            r.update(bound="hbm", achieved=a, peak=hbm, unit="GB/s", frac=a / hbm, peak_source="measured (copy)")
+        elif name == "oz_gemm":
+            a = v["flops"] / t / 1e12
+            r.update(bound="tensor", achieved=a, peak=bf16 / 21.0, unit="TFLOP/s", frac=a * 21.0 / bf16,
+                     peak_source="measured sustained bf16 / 21 (FP64-equivalent peak of the six-slice split "
+                                 "product)", executed_bf16_tflops=21.0 * a)
+        elif v["flops"] > 0:
+            a = v["flops"] / t / 1e12
+            f32 = name.endswith("f32>") or "<float" in name
+            pkv = FP32_PEAK_TFLOPS_DERIVED if f32 else FP64_PEAK_TFLOPS_NOMINAL
+            r.update(bound="alu", achieved=a, peak=pkv, unit="TFLOP/s", frac=a / pkv,
+                     peak_source=("derived FP32: 152 SMs x 128 lanes x 2 flop x 2.07 GHz" if f32 else
+                                  "nominal FP64 of GB300, 1.25 TFLOP/s (no measured FP64 peak)"))
+        else:
+            r.update(bound="latency", achieved=None, peak=None, unit=None, frac=None)
+        out.append(r)
+    return out
 
 
 def max_over_ranks(dist, ms, device):
@@ -338,6 +381,40 @@ def run_reference(args):
                            for q, m in enumerate(mats)],
             "e2e": {"value": v, "unit": "projections/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def admm_maxcut64(sdpgpu, stream, reps=2, rr=0, oracle_too=True):
+    """ADMM solves/s on max-cut n = 64, p = 0.1 (rho = 1, residual 1e-4):
+    the mixed path, the plain FP64 path and the exact-eigendecomposition
+    comparator (own GPU Jacobi), each timed over `reps` solves after one
+    untimed solve (host clock around sdp_solve, which returns after the
+    solve), objective against the FP64 oracle; the oracle timed on one
+    host core."""
+    import importlib
+    importlib.import_module("oracle.build").build()
+    import oracle
+    inst = gen.workload_maxcut64(0)
+    cons = oracle.Constraints(inst.n, inst.m, inst.cp, inst.ci, inst.cj, inst.cv)
+    t0 = time.perf_counter()
+    ref = oracle.admm_solve(inst.n, inst.C, cons, inst.b, eps_abs=1e-4)
+    t_or = time.perf_counter() - t0
+    out = {"workload": "max-cut n=64 p=0.1 (seeded), rho=1, residual 1e-4, max 5000 iterations",
+           "metric": "ADMM solves/s"}
+    for name, kw in [("mixed", dict(precision=sdpgpu.PREC_BF16X3)), ("fp64", dict(precision=sdpgpu.PREC_FP64)),
+                     ("exact_eig_fp64", dict(precision=sdpgpu.PREC_FP64, exact_only=1))]:
+        c = sdpgpu.Context(stream=stream, eps_abs=1e-4, rr_method=rr, **kw).setup(inst)
+        c.solve()
+        t0 = time.perf_counter()
+        for _ in range(max(1, reps)):
+            r = c.solve()
+        dt = (time.perf_counter() - t0) / max(1, reps)
+        out[name] = {"solves_per_s": 1.0 / dt, "ms_per_solve": 1000 * dt, "iters": r["iters"],
+                     "ms_per_iter": 1000 * dt / max(1, r["iters"]), "status": r["status_name"], "obj": r["obj"],
+                     "rel_obj_err_vs_oracle": abs(r["obj"] - ref["obj"]) / abs(ref["obj"]),
+                     "n_lobpcg": r["n_lobpcg"], "n_exact": r["n_exact"], "n_ladder": r.get("n_ladder")}
+    out["oracle_exact_cpu"] = {"solves_per_s": 1.0 / t_or, "iters": ref["iters"], "obj": ref["obj"], "cores": 1}
+    out["mixed_vs_fp64_path"] = out["mixed"]["solves_per_s"] / out["fp64"]["solves_per_s"]
+    return out
 
 
 def _ctx_for(sdpgpu, inst, stream, prec, **kw):
@@ -573,45 +650,17 @@ def main():
     total_ms = max_over_ranks(dist, sum(step_ms), "cuda")
     value = whole_job_rate(len(mats) * args.steps, world, total_ms)
     launches = sum(v["launches"] for v in prof.values())
-    # roofline of the dominant kernel family (largest summed event time)
-    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    # roofline of the dominant kernel (largest summed event time per named
+    # kernel or launch group), each against the peak of the unit that bounds it
+    named = sdpgpu.prof_named()
     pk = peaks()
-    rr = prof["rayleigh_ritz"]
-    prod = prof["product"]
-    ach = prod["flops"] / (prod["ms"] / 1000.0) / 1e12 if prod["ms"] > 0 else 0.0
-    if args.prec == "fp64":
-        roof = {"kernel": "k_gemm<NN,double> (W times block, FP64 CUDA cores)", "bound": "alu",
-                "achieved": ach, "peak": FP64_PEAK_TFLOPS_NOMINAL, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_TFLOPS_NOMINAL, "traffic": None,
-                "peak_source": "nominal FP64 of GB300 (1.25 TFLOP/s; 1.20 measured by an FMA loop)",
-                "launches": prod["launches"], "avg_launch_ms": prod["ms"] / max(prod["timed"], 1)}
-    else:
-        gbs = prod["bytes"] / (prod["ms"] / 1000.0) / 1e9 if prod["ms"] > 0 else 0.0
-        peak = pk.get("hbm_gbs", 6800.0)
-        roof = {"kernel": "tcgen05 split-BF16x3 product", "bound": "hbm", "achieved": gbs, "peak": peak,
-                "unit": "GB/s", "frac": gbs / peak, "traffic": None, "launches": prod["launches"],
-                "avg_launch_ms": prod["ms"] / max(prod["timed"], 1)}
-    roof["share_of_step"] = {k: round(v["ms"] / max(total_ms, 1e-9), 4) for k, v in prof.items() if v["ms"] > 0}
-    roof["dominant_family"] = dom[0]
-    if dom[0] == "rayleigh_ritz" and rr["ms"] > 0:
-        # the step is the Rayleigh-Ritz eigensolver: FP32 (mixed) or FP64
-        # CUDA-core arithmetic behind block and grid barriers
-        rr_tf = rr["flops"] / (rr["ms"] / 1000.0) / 1e12
-        if args.prec == "fp64":
-            peak_rr, src = FP64_PEAK_TFLOPS_NOMINAL, "nominal FP64 of GB300 (1.20 measured by an FMA loop)"
-        else:
-            peak_rr = FP32_PEAK_TFLOPS_DERIVED
-            src = "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz"
-        rr_roof = {"kernel": "Rayleigh-Ritz eigensolver (k_rr_tri, k_trid_coop, k_trid_backtr, k_chol_inv_coop, "
-                             "k_gemm; algorithmic flops per launch)", "bound": "alu", "achieved": rr_tf,
-                   "peak": peak_rr, "unit": "TFLOP/s", "frac": rr_tf / peak_rr, "traffic": None,
-                   "peak_source": src, "launches": rr["launches"],
-                   "avg_launch_ms": rr["ms"] / max(rr["timed"], 1),
-                   "share_of_step": roof["share_of_step"], "dominant_family": dom[0]}
-        roof.pop("share_of_step")
-        roof.pop("dominant_family")
-        rr_roof["product_roofline"] = roof
-        roof = rr_roof
+    kern = kernel_rooflines(named, pk, total_ms)
+    roof = dict(kern[0]) if kern else {}
+    roof["share_of_step_by_family"] = {k: round(v["ms"] / max(total_ms, 1e-9), 4)
+                                       for k, v in prof.items() if v["ms"] > 0}
+    roof["top_kernels"] = kern[1:8]
+    tcp = [r for r in kern if r["kernel"] == "k_tc_wprod"]
+    roof["product_roofline"] = tcp[0] if tcp else None
     # the plain FP64 GPU path on the same sweep (one step after one warm-up)
     fp64_path = None
     if args.prec != "fp64" and not args.no_fp64_path and rank == 0:
@@ -653,6 +702,9 @@ def main():
         steps = max(1, args.steps)
         e2e = {"value": len(mats) * steps / dt, "unit": "projections/s", "h2d_bytes_per_step": h2d // steps,
                "d2h_bytes_per_step": d2h // steps}
+    admm0 = None
+    if rank == 0 and not args.no_admm:
+        admm0 = admm_maxcut64(sdpgpu, stream, reps=2, rr=args.rr)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_oracle_rate(mats)
@@ -663,16 +715,21 @@ def main():
         line = {"metric": "PSD projections/s (warm-started LOBPCG, k/n sweep)", "value": value,
                 "unit": "projections/s", "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
                 "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else "bf16x3+f32+f64",
+                "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else "bf16x3+f64",
                 "data": "synthetic",
                 "config": {"workload": "psd_projection_sweep",
                            "matrices": ["n=%d k/n=%g" % (m["n"], m["f"]) for m in mats],
                            "precision": args.prec,
                            "rayleigh_ritz": "fp64" if (args.prec == "fp64" or args.rr_prec == "fp64") else "fp32",
+                           "arithmetic": ("FP64 CUDA cores throughout" if args.prec == "fp64" else
+                                          "W S split-BF16x3 on tcgen05 (FP32 accumulate), raised to the "
+                                          "FP64-accurate split product by the precision ladder; Rayleigh-Ritz "
+                                          "FP64-accurate (split-product tensor-core GEMMs + FP64 CUDA cores); "
+                                          "residuals FP64"),
                            "l2": "flushed between steps (256 MiB write)",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "fp64_path": fp64_path, "rate_on_oracle_sample": gpu_on_sample,
+                "fp64_path": fp64_path, "rate_on_oracle_sample": gpu_on_sample, "admm_maxcut64": admm0,
                 "speedup_vs_fp64_path": (value / fp64_path["value"]) if fp64_path else None,
                 "clocks": ck, "max_rel_err_vs_closed_form": max(errs),
                 "per_matrix": [{"n": m["n"], "k": m["k"], "ms": round(per_ms[q], 3), "rel_err": errs[q],

@@ -330,6 +330,10 @@ void sdp_prof_enable(int on);
 void sdp_prof_reset(void);
 /* synchronise the pending events and copy one family's counters */
 int sdp_prof_get(int family, sdp_prof_entry* out);
+/* the same counters per named kernel (or named launch group), in name
+ * order: entry idx (0-based) with its name copied into name[name_cap];
+ * SDP_E_INVALID past the last one */
+int sdp_prof_named(int idx, char* name, int name_cap, sdp_prof_entry* out);
 
 #ifdef __cplusplus
 }

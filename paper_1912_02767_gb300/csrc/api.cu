@@ -68,6 +68,21 @@ extern "C" void sdp_prof_reset(void) {
     P.launches[f] = P.timed[f] = 0;
     P.ms[f] = P.flops[f] = P.bytes[f] = 0.0;
   }
+  P.named.clear();
+}
+extern "C" int sdp_prof_named(int idx, char* name, int name_cap, sdp_prof_entry* out) {
+  Prof& P = prof();
+  P.flush();
+  if (idx < 0 || idx >= (int)P.named.size() || !out) return SDP_E_INVALID;
+  auto it = P.named.begin();
+  std::advance(it, idx);
+  if (name && name_cap > 0) snprintf(name, (size_t)name_cap, "%s", it->first.c_str());
+  out->launches = it->second.launches;
+  out->ms = it->second.ms;
+  out->timed = it->second.timed;
+  out->flops = it->second.flops;
+  out->bytes = it->second.bytes;
+  return SDP_OK;
 }
 extern "C" int sdp_prof_get(int fam, sdp_prof_entry* out) {
   if (fam < 0 || fam >= SDP_PROF_FAMILIES || !out) return SDP_E_INVALID;

@@ -4,6 +4,8 @@
 #include <stdio.h>
 #include <stdlib.h>
 
+#include <map>
+#include <string>
 #include <vector>
 
 namespace sdpg {
@@ -12,6 +14,13 @@ struct ProfPending {
   int fam;
   cudaEvent_t a, b;
   double flops, bytes;
+  const char* name;
+};
+
+// counters of one named kernel (or launch group)
+struct ProfNamed {
+  long long launches = 0, timed = 0;
+  double ms = 0.0, flops = 0.0, bytes = 0.0;
 };
 
 struct Prof {
@@ -23,6 +32,7 @@ struct Prof {
   double bytes[10] = {};
   std::vector<ProfPending> pending;
   std::vector<cudaEvent_t> pool;
+  std::map<std::string, ProfNamed> named;
   cudaEvent_t get() {
     cudaEvent_t e;
     if (!pool.empty()) {
@@ -39,6 +49,13 @@ struct Prof {
       if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) {
         ms[p.fam] += t;
         timed[p.fam]++;
+        if (p.name && *p.name) {
+          ProfNamed& q = named[p.name];
+          q.ms += t;
+          q.timed++;
+          q.flops += p.flops;
+          q.bytes += p.bytes;
+        }
       }
       pool.push_back(p.a);
       pool.push_back(p.b);
@@ -62,6 +79,7 @@ struct ProfScope {
     P.launches[fam]++;
     P.flops[fam] += fl;
     P.bytes[fam] += by;
+    if (name && *name) P.named[name].launches++;
     if (P.on) {
       a = P.get();
       cudaEventRecord(a, s);
@@ -79,7 +97,7 @@ struct ProfScope {
     if (a) {
       cudaEvent_t b = P.get();
       cudaEventRecord(b, s);
-      P.pending.push_back({fam, a, b, fl, by});
+      P.pending.push_back({fam, a, b, fl, by, name});
       if (P.pending.size() > 8192) P.flush();
     }
   }

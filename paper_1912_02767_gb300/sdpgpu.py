@@ -104,6 +104,7 @@ def load():
     L.sdp_prof_enable.restype = None
     L.sdp_prof_reset.restype = None
     L.sdp_prof_get.argtypes = [C.c_int, C.POINTER(ProfEntry)]
+    L.sdp_prof_named.argtypes = [C.c_int, C.c_char_p, C.c_int, C.POINTER(ProfEntry)]
     _lib = L
     return L
 
@@ -130,6 +131,22 @@ def prof_get():
 def set_wait_limit(seconds):
     """sdp_set_wait_limit: limit of every bounded device wait (0 = default)."""
     return load().sdp_set_wait_limit(float(seconds))
+
+
+def prof_named():
+    """Per named kernel: launches, timed event ms, algorithmic flops and bytes."""
+    L = load()
+    out = {}
+    buf = C.create_string_buffer(128)
+    idx = 0
+    while True:
+        e = ProfEntry()
+        if L.sdp_prof_named(idx, buf, 128, C.byref(e)) != 0:
+            break
+        out[buf.value.decode()] = {"launches": e.launches, "ms": e.ms, "timed": e.timed, "flops": e.flops,
+                                   "bytes": e.bytes}
+        idx += 1
+    return out
 
 
 def status_str(code):
