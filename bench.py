@@ -386,7 +386,7 @@ def run_reference(args):
 def admm_maxcut64(sdpgpu, stream, reps=2, rr=0, oracle_too=True):
     """ADMM solves/s on max-cut n = 64, p = 0.1 (rho = 1, residual 1e-4):
     the mixed path, the plain FP64 path and the exact-eigendecomposition
-    comparator (own GPU Jacobi), each timed over `reps` solves after one
+    comparators (own GPU Jacobi; cuSOLVER syevd), each timed over `reps` solves after one
     untimed solve (host clock around sdp_solve, which returns after the
     solve), objective against the FP64 oracle; the oracle timed on one
     host core."""
@@ -401,7 +401,8 @@ def admm_maxcut64(sdpgpu, stream, reps=2, rr=0, oracle_too=True):
     out = {"workload": "max-cut n=64 p=0.1 (seeded), rho=1, residual 1e-4, max 5000 iterations",
            "metric": "ADMM solves/s"}
     for name, kw in [("mixed", dict(precision=sdpgpu.PREC_BF16X3)), ("fp64", dict(precision=sdpgpu.PREC_FP64)),
-                     ("exact_eig_fp64", dict(precision=sdpgpu.PREC_FP64, exact_only=1))]:
+                     ("exact_eig_fp64", dict(precision=sdpgpu.PREC_FP64, exact_only=1)),
+                     ("exact_syevd_fp64", dict(precision=sdpgpu.PREC_FP64, exact_only=1, exact_solver=1))]:
         c = sdpgpu.Context(stream=stream, eps_abs=1e-4, rr_method=rr, **kw).setup(inst)
         c.solve()
         t0 = time.perf_counter()

@@ -98,6 +98,11 @@ typedef struct {
                        /* eigenvectors of the positive eigenvalues of W); 1 negative mode  */
                        /* (Section 5: V_warm approximates those of the negative ones;     */
                        /* LOBPCG runs on -W and Pi(W) = W + Pi(-W))          default 0     */
+  int exact_solver;    /* eigensolver of the exact branch (Section 1's full                */
+                       /* eigendecomposition; with exact_only = 1 the exact-eig ADMM       */
+                       /* comparator): 0 the library's parallel cyclic Jacobi, 1 the      */
+                       /* cuSOLVER syevd library routine (a comparator, not the hot path)  */
+                       /*                                                    default 0     */
 } sdp_settings;
 
 typedef struct {

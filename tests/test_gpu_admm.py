@@ -57,6 +57,18 @@ def test_exact_only_matches_oracle_iterates(sdp, orc):
     assert np.abs(X - ref["x"]).max() <= 1e-7
 
 
+def test_exact_syevd_comparator_matches_oracle_iterates(sdp, orc):
+    """The exact-eigendecomposition comparator through the cuSOLVER syevd
+    library routine (exact_solver = 1) runs the oracle's exact-projection
+    iteration as closely as the built-in Jacobi does."""
+    inst = gen.maxcut(24, 0.3, np.random.default_rng(3))
+    ref = orc.admm_solve(inst.n, inst.C, cons_of(orc, inst), inst.b, eps_abs=1e-5, check_every=10)
+    c, res, X, y, S = gpu_solve(sdp, inst, eps_abs=1e-5, check_every=10, exact_only=1, exact_solver=1)
+    assert res["status_name"] == "SOLVED" and res["iters"] == ref["iters"]
+    assert abs(res["obj"] - ref["obj"]) <= 1e-8 * abs(ref["obj"])
+    assert np.abs(X - ref["x"]).max() <= 1e-7
+
+
 @pytest.mark.parametrize("seed", [0, 1])
 def test_maxcut_brute_force_and_closed_forms(sdp, seed):
     rng = np.random.default_rng(seed)
