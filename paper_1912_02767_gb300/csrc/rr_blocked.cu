@@ -82,14 +82,29 @@ __global__ void __launch_bounds__(1024) k_potrf_inv_block(double* G, int ldg, do
   }
   for (int j = tid; j < bb; j += nt) xd[j] = 1.0 / A[j][j];
   __syncthreads();
-  // X = L^{-1}: column j solves L x = e_j; X[i][j] kept at A[j][i] (i > j)
+  // X = L^{-1}: column j solves L x = e_j by forward substitution in axpy
+  // form, one column per warp: once x_k is known, the rows below take
+  // -L_ik x_k (lane-parallel FMAs, no reductions -- an FP64 warp instruction
+  // costs the SM's FP64 pipe tens of cycles).  X[i][j] is kept at A[j][i].
   for (int j = wid; j < bb; j += nw) {
-    for (int i = j + 1; i < bb; ++i) {
-      double acc = lane == 0 ? A[i][j] * xd[j] : 0.0;  // k = j term: L_ij X_jj
-      for (int k = j + 1 + lane; k < i; k += 32) acc += A[i][k] * A[j][k];
-      acc = warp_sum_d(acc);
-      if (lane == 0) A[j][i] = -acc * xd[i];
-      __syncwarp();
+    double acc[kBlk / 32];  // running sums of the rows this lane owns: rows i = lane + 32 q
+#pragma unroll
+    for (int q = 0; q < kBlk / 32; ++q) acc[q] = 0.0;
+    for (int k = j; k < bb; ++k) {
+      // x_k = (delta_jk - sum_{j <= l < k} L_kl x_l) / L_kk, held by the lane owning row k
+      double xk = 0.0;
+      double ak = 0.0;
+#pragma unroll
+      for (int q = 0; q < kBlk / 32; ++q)  // register select, no local-memory indexing
+        if (q == (k >> 5)) ak = acc[q];
+      if (lane == (k & 31)) xk = ((k == j ? 1.0 : 0.0) - ak) * xd[k];
+      xk = __shfl_sync(0xffffffffu, xk, k & 31);
+      if (lane == 0) A[j][k] = xk;  // diagonal entry too (overwritten with xd below)
+#pragma unroll
+      for (int q = 0; q < kBlk / 32; ++q) {
+        const int i = lane + 32 * q;
+        if (i > k && i < bb) acc[q] += A[i][k] * xk;
+      }
     }
   }
   __syncthreads();
