@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--workload", default="sweep", choices=["sweep", "maxcut64", "theta500", "batch", "serve"],
                     help="sweep: the projection sweep (the bench line); the others time ADMM solves")
     ap.add_argument("--count", type=int, default=64, help="instances (batch) or requests (serve)")
+    ap.add_argument("--max-iter", type=int, default=20000, help="ADMM iteration limit of the theta500 workload")
+    ap.add_argument("--both-precisions", action="store_true", help="theta500: run the FP64 path too")
     ap.add_argument("--serve-seconds", type=float, default=0.0,
                     help="serve: stop after this wall time and report the requests completed so far "
                          "(0: run every request to completion)")
@@ -467,14 +469,27 @@ def run_admm(args):
         out["oracle_exact_cpu"] = {"solves_per_s": 1.0 / t_or, "iters": ref["iters"], "obj": ref["obj"], "cores": 1}
     elif args.workload == "theta500":
         inst = gen.workload_theta500(0)
-        for name, prec in [("mixed", PMX), ("fp64", P64)]:
-            c = sdpgpu.Context(stream=stream, precision=prec, eps_abs=1e-4, rho=10.0, rr_method=args.rr).setup(inst)
+        gold = None
+        gp = os.path.join(ROOT, "tests", "golden", "theta500_objective.json")
+        if os.path.exists(gp):
+            gold = json.load(open(gp))
+            out["oracle"] = {k: gold[k] for k in ("status", "iters", "obj", "r_prim", "r_dual", "seconds")}
+        precs = [("mixed", PMX)] if args.prec == "bf16x3" else [("fp64", P64)]
+        if args.both_precisions:
+            precs = [("mixed", PMX), ("fp64", P64)]
+        for name, prec in precs:
+            c = sdpgpu.Context(stream=stream, precision=prec, eps_abs=1e-4, rho=10.0, rr_method=args.rr,
+                               max_iter=args.max_iter).setup(inst)
             t0 = time.perf_counter()
             r = c.solve()
             dt = time.perf_counter() - t0
             out[name] = {"solves_per_s": 1.0 / dt, "s": dt, "iters": r["iters"], "status": r["status_name"],
                          "obj": r["obj"], "r_prim": r["r_prim"], "r_dual": r["r_dual"], "rank": r["rank"],
-                         "n_lobpcg": r["n_lobpcg"], "n_exact": r["n_exact"]}
+                         "n_lobpcg": r["n_lobpcg"], "n_exact": r["n_exact"], "n_ladder": r["n_ladder"],
+                         "ms_per_iter": 1000 * dt / max(1, r["iters"])}
+            if gold:
+                out[name]["rel_obj_err_vs_oracle"] = abs(r["obj"] - gold["obj"]) / abs(gold["obj"])
+            print("%s: %s" % (name, json.dumps(out[name])), file=sys.stderr, flush=True)
     elif args.workload == "batch":
         insts = gen.workload_batch(args.count)
         ctxs = [_ctx_for(sdpgpu, i, stream, PMX, eps_abs=1e-4, rr_method=args.rr) for i in insts]
