@@ -47,6 +47,8 @@ def parse():
                     help="sweep: the projection sweep (the bench line); the others time ADMM solves")
     ap.add_argument("--count", type=int, default=64, help="instances (batch) or requests (serve)")
     ap.add_argument("--max-iter", type=int, default=20000, help="ADMM iteration limit of the theta500 workload")
+    ap.add_argument("--serve-maxcut-n", type=int, default=2000, help="serve: largest max-cut request n")
+    ap.add_argument("--serve-theta-n", type=int, default=1000, help="serve: largest theta request n")
     ap.add_argument("--both-precisions", action="store_true", help="theta500: run the FP64 path too")
     ap.add_argument("--serve-seconds", type=float, default=0.0,
                     help="serve: stop after this wall time and report the requests completed so far "
@@ -500,29 +502,30 @@ def run_admm(args):
                                 "statuses": {k: sum(1 for i in infos if i["status_name"] == k)
                                              for k in set(i["status_name"] for i in infos)},
                                 "iters_max": max(i["iters"] for i in infos)}
+        out["mixed_batched"]["n_ladder_total"] = sum(i.get("n_ladder", 0) for i in infos)
         print("batched: %s" % json.dumps(out["mixed_batched"]), file=sys.stderr, flush=True)
-        # one at a time (same mixed path) on a subset, then the plain FP64 path
-        sub = sorted(range(len(insts)), key=lambda q: insts[q].n)[:4]
-        t0 = time.perf_counter()
-        alone = []
-        for q in sub:
-            alone.append(ctxs[q].solve())
-        dt1 = time.perf_counter() - t0
-        out["mixed_one_at_a_time"] = {"solves_per_s": len(sub) / dt1, "instances": [insts[q].n for q in sub],
-                                      "same_as_batched": all(abs(a["obj"] - infos[q]["obj"]) <= 1e-9 * abs(a["obj"])
-                                                             and a["iters"] == infos[q]["iters"]
-                                                             for a, q in zip(alone, sub))}
-        print("one-at-a-time: %s" % json.dumps(out["mixed_one_at_a_time"]), file=sys.stderr, flush=True)
-        c64 = [_ctx_for(sdpgpu, insts[q], stream, P64, eps_abs=1e-4, rr_method=args.rr) for q in sub[:2]]
-        t0 = time.perf_counter()
-        r64 = [c.solve() for c in c64]
-        dt2 = time.perf_counter() - t0
-        out["fp64_one_at_a_time"] = {"solves_per_s": len(c64) / dt2, "instances": [insts[q].n for q in sub[:2]],
-                                     "rel_obj_vs_mixed": [abs(a["obj"] - infos[q]["obj"]) / abs(a["obj"])
-                                                          for a, q in zip(r64, sub[:2])]}
+        # one at a time on a stratified subset (quartile midpoints in n), the
+        # same mixed path and the plain FP64 path: throughput estimates of
+        # one-solve-at-a-time on this size distribution
+        order = sorted(range(len(insts)), key=lambda q: insts[q].n)
+        sub = sorted(set(order[min(len(order) - 1, int((j + 0.5) * len(order) / 4))] for j in range(4)))
+        for name, prec in [("mixed_one_at_a_time", PMX), ("fp64_one_at_a_time", P64)]:
+            cs1 = [_ctx_for(sdpgpu, insts[q], stream, prec, eps_abs=1e-4, rr_method=args.rr) for q in sub]
+            t0 = time.perf_counter()
+            rs = [c.solve() for c in cs1]
+            dt1 = time.perf_counter() - t0
+            out[name] = {"solves_per_s": len(sub) / dt1, "instances_n": [insts[q].n for q in sub],
+                         "statuses": [r["status_name"] for r in rs], "iters": [r["iters"] for r in rs],
+                         "same_as_batched": [abs(r["obj"] - infos[q]["obj"]) <= 1e-9 * abs(r["obj"])
+                                             and r["iters"] == infos[q]["iters"] for r, q in zip(rs, sub)],
+                         "rel_obj_vs_batched": [abs(r["obj"] - infos[q]["obj"]) / abs(r["obj"]) for r, q in
+                                                zip(rs, sub)]}
+            print("%s: %s" % (name, json.dumps(out[name])), file=sys.stderr, flush=True)
+        out["batched_vs_fp64_one_at_a_time"] = (out["mixed_batched"]["solves_per_s"] /
+                                                out["fp64_one_at_a_time"]["solves_per_s"])
         out["n_range"] = [min(i.n for i in insts), max(i.n for i in insts)]
     elif args.workload == "serve":
-        reqs = gen.workload_serving(args.count, maxcut_n=(100, 600), theta_n=(100, 300))
+        reqs = gen.workload_serving(args.count, maxcut_n=(100, args.serve_maxcut_n), theta_n=(100, args.serve_theta_n))
         kw = dict(eps_abs=1e-4, tol_coef=0.1, precision=PMX)
         srv = sdpgpu.Server(budget_bytes=64 << 30, max_slots=32, iters_per_step=100, stream=stream, **kw)
         ctxs, tickets, arrive, done_t = {}, {}, {}, {}
