@@ -50,6 +50,12 @@ def parse():
     ap.add_argument("--serve-maxcut-n", type=int, default=2000, help="serve: largest max-cut request n")
     ap.add_argument("--serve-theta-n", type=int, default=1000, help="serve: largest theta request n")
     ap.add_argument("--both-precisions", action="store_true", help="theta500: run the FP64 path too")
+    ap.add_argument("--profile-iters", type=int, default=0,
+                    help="theta500/maxcut64: one more solve capped at this many iterations with the per-kernel "
+                         "event timers on; reports wall time against summed kernel time and the top kernels")
+    ap.add_argument("--exact-eps", default="",
+                    help="theta500: also solve with exact FP64 eigendecompositions (cuSOLVER syevd) at these "
+                         "residual tolerances (comma list, e.g. 1e-4,1e-6); the tightest is the reference objective")
     ap.add_argument("--serve-seconds", type=float, default=0.0,
                     help="serve: stop after this wall time and report the requests completed so far "
                          "(0: run every request to completion)")
@@ -203,6 +209,32 @@ def kernel_rooflines(named, pk, total_ms):
             r.update(bound="latency", achieved=None, peak=None, unit=None, frac=None)
         out.append(r)
     return out
+
+
+def profile_solve(sdpgpu, stream, inst, iters, kw):
+    """One solve capped at `iters` ADMM iterations with the event timers on:
+    wall time, summed kernel event time and the largest kernels.  The events
+    serialise launches, so this is a breakdown, not a throughput figure."""
+    import torch
+    c = sdpgpu.Context(stream=stream, max_iter=iters, **kw).setup(inst)
+    torch.cuda.synchronize()
+    sdpgpu.prof_reset()
+    sdpgpu.prof_enable(True)
+    t0 = time.perf_counter()
+    try:
+        r = c.solve()
+        torch.cuda.synchronize()
+    finally:
+        sdpgpu.prof_enable(False)
+    wall = 1000.0 * (time.perf_counter() - t0)
+    named = sdpgpu.prof_named()
+    dev = sum(v["ms"] for v in named.values())
+    top = sorted(named.items(), key=lambda kv: -kv[1]["ms"])[:14]
+    return {"iters": r["iters"], "wall_ms": round(wall, 1), "kernel_ms": round(dev, 1),
+            "launches": sum(v["launches"] for v in named.values()), "n_lobpcg": r["n_lobpcg"],
+            "n_ladder": r["n_ladder"],
+            "top": [{"kernel": k, "ms": round(v["ms"], 2), "launches": v["launches"],
+                     "share_of_wall": round(v["ms"] / max(wall, 1e-9), 4)} for k, v in top]}
 
 
 def max_over_ranks(dist, ms, device):
@@ -492,6 +524,28 @@ def run_admm(args):
             if gold:
                 out[name]["rel_obj_err_vs_oracle"] = abs(r["obj"] - gold["obj"]) / abs(gold["obj"])
             print("%s: %s" % (name, json.dumps(out[name])), file=sys.stderr, flush=True)
+        if args.profile_iters > 0:
+            out["profile"] = profile_solve(sdpgpu, stream, inst, args.profile_iters,
+                                           dict(precision=precs[0][1], eps_abs=1e-4, rho=10.0, rr_method=args.rr))
+            print("profile: %s" % json.dumps(out["profile"]), file=sys.stderr, flush=True)
+        # exact-projection solves: how far the objective at residual 1e-4 can
+        # sit from the optimum (the tightest tolerance stands for the optimum)
+        eps_list = sorted((float(e) for e in args.exact_eps.split(",") if e), reverse=True)
+        for eps in eps_list:
+            c = sdpgpu.Context(stream=stream, precision=P64, exact_only=1, exact_solver=1, eps_abs=eps, rho=10.0,
+                               max_iter=args.max_iter).setup(inst)
+            t0 = time.perf_counter()
+            r = c.solve()
+            dt = time.perf_counter() - t0
+            key = "exact_syevd_fp64_eps%g" % eps
+            out[key] = {"s": dt, "iters": r["iters"], "status": r["status_name"], "obj": r["obj"],
+                        "r_prim": r["r_prim"], "r_dual": r["r_dual"], "rank": r["rank"],
+                        "ms_per_iter": 1000 * dt / max(1, r["iters"])}
+            print("%s: %s" % (key, json.dumps(out[key])), file=sys.stderr, flush=True)
+        if eps_list:
+            ref = out["exact_syevd_fp64_eps%g" % eps_list[-1]]["obj"]
+            out["rel_obj_vs_tightest_exact"] = {k: abs(v["obj"] - ref) / abs(ref) for k, v in out.items()
+                                                if isinstance(v, dict) and "obj" in v}
     elif args.workload == "batch":
         insts = gen.workload_batch(args.count)
         ctxs = [_ctx_for(sdpgpu, i, stream, PMX, eps_abs=1e-4, rr_method=args.rr) for i in insts]

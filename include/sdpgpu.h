@@ -103,6 +103,11 @@ typedef struct {
                        /* comparator): 0 the library's parallel cyclic Jacobi, 1 the      */
                        /* cuSOLVER syevd library routine (a comparator, not the hot path)  */
                        /*                                                    default 0     */
+  int soft_lock;       /* 0: every residual and Delta X column enters the trial subspace  */
+                       /* span(X, R, Delta X) of each step, as in Algorithm 3; 1: columns  */
+                       /* whose residual is already within tol are left out (soft locking:*/
+                       /* a narrower Rayleigh-Ritz step, but the converged pairs are not  */
+                       /* improved further)                                  default 0     */
 } sdp_settings;
 
 typedef struct {

@@ -122,6 +122,7 @@ extern "C" void sdp_default_settings(sdp_settings* s) {
   s->rr_fp32 = 0;
   s->proj_neg = 0;
   s->exact_solver = 0;
+  s->soft_lock = 0;
 }
 
 extern "C" const char* sdp_status_str(int s) {
@@ -146,7 +147,7 @@ extern "C" const char* sdp_status_str(int s) {
 static bool settings_ok(const sdp_settings* s) {
   return s->rho > 0 && s->sigma > 0 && s->alpha > 0 && s->alpha < 2 && s->eps_abs >= 0 && s->eps_rel >= 0 &&
          s->max_iter >= 1 && s->check_every >= 1 && s->lobpcg_max_iter >= 1 && s->precision >= 0 &&
-         s->precision <= 2 && (s->rr_method == 0 || s->rr_method == 1) && (s->rr_fp32 == 0 || s->rr_fp32 == 1) && (s->proj_neg == 0 || s->proj_neg == 1) && (s->exact_solver == 0 || s->exact_solver == 1) && s->tol_coef > 0 && s->expand_frac > 0 && s->mode_frac > 0 && s->mode_frac <= 0.5;
+         s->precision <= 2 && (s->rr_method == 0 || s->rr_method == 1) && (s->rr_fp32 == 0 || s->rr_fp32 == 1) && (s->proj_neg == 0 || s->proj_neg == 1) && (s->exact_solver == 0 || s->exact_solver == 1) && (s->soft_lock == 0 || s->soft_lock == 1) && s->tol_coef > 0 && s->expand_frac > 0 && s->mode_frac > 0 && s->mode_frac <= 0.5;
 }
 
 // ---------------------------------------------------------------------------

@@ -67,6 +67,8 @@ struct Ctl {
   int snap;      // 1: keep x, Y, y_e of this iteration (termination check follows)
   int ma;        // residual columns still active (not yet within tol)
   int mPa;       // Delta X columns of active Ritz pairs
+  int soft_lock; // 1: pairs within tol leave R and Delta X of the next step
+  int spare_;
   double tol;    // LOBPCG residual tolerance
   double res_max;  // largest Ritz residual norm of the block
   double res_pos2; // sum of squared residual norms of the positive pairs

@@ -65,6 +65,7 @@ __host__ __device__ inline size_t rr_tri_smem_bytes(int p, int zk, int tsize) {
 constexpr size_t kRRTriSmemMax = 231936;  // 227 KiB per CTA less the kernel's static shared memory
 // threads of a k_rr_tri CTA for widths up to p (p <= threads): fewer warps
 // per barrier for narrow subspaces, all 32 for wide ones
+constexpr int kRRTriMaxF64 = 96;  // widest FP64 trial subspace on the one-CTA route
 inline int rr_tri_threads(int p) { return p <= 32 ? 128 : (p <= 64 ? 256 : (p <= 128 ? 512 : 1024)); }
 __global__ void k_resid(Inst* insts, WorkMap wm);
 __global__ void k_resid_finish(Inst* insts, const int* list, int last_allowed);
@@ -94,6 +95,18 @@ __global__ void k_latrd_coop(double* A, int p, int keep, int j0, int j1, double*
                              double* pt, double* vb, GridBar* b);
 __global__ void k_latrd_wfinal(const double* Vp, double* Wp, const double* Kg, int p, int r0, int nc);
 __global__ void k_sym_copy(const double* H, double* A, int p);
+// Householder tridiagonalization on one thread-block cluster (distributed
+// shared memory); host side: cluster width for p (16, 8, or 0 = does not
+// fit) and the launch (0 ok, -1 refused)
+constexpr int kTridClThreads = 512;
+constexpr size_t kTridClSmemMax = 230400;
+__host__ __device__ inline size_t trid_cluster_smem(int p, int cl) {
+  const int ncl = (p + cl - 1) / cl, ldl = p | 1;
+  return ((size_t)ncl * ldl + 6 * (size_t)p + 8 + kTridClThreads + 32) * sizeof(double);
+}
+int trid_cluster_width(int p);
+int trid_cluster_max_p(int cl);
+int trid_cluster(cudaStream_t s, int cl, const double* H, double* A, int p, int keep, double* vb, GridBar* b);
 template <typename TS, typename T>
 __global__ void k_trid_eig(double* vb, int p, int keep, int S, int refine, int final, double* theta, int* npos,
                            const GridBar* b);
@@ -112,6 +125,12 @@ constexpr size_t kBacktrSmemMax = 230400;  // 227 KiB per CTA less the kernel's 
 // their products on the tensor cores)
 constexpr int kBlk = 128;  // diagonal block / reflector block width
 constexpr size_t kBlkSmem = (size_t)kBlk * (kBlk + 1) * sizeof(double);
+// diagonal block of the blocked Cholesky/inverse: narrower than kBlk, since
+// its O(b^3) FP64 work runs on one SM while the panel and trailing products
+// run on the tensor cores
+constexpr int kPotrfBlk = 64;
+constexpr size_t potrf_block_smem(int blk) { return (size_t)blk * (blk + 1) * sizeof(double); }
+template <int BLK>
 __global__ void k_potrf_inv_block(double* G, int ldg, double* Linv, int ldl, int j0, int bb, double piv_min,
                                   GridBar* bar);
 __global__ void k_wy_vmat(const double* A, int p, int nref, double* V);

@@ -310,7 +310,7 @@ __global__ void k_resid_finish(Inst* insts, const int* list, int last_allowed) {
       ++npos;
       rpos2 += r * r;
     }
-    bool act = fresh || r > c->tol;
+    bool act = fresh || !c->soft_lock || r > c->tol;  // Algorithm 3: every residual (soft locking: the unconverged)
     I.slot[j] = act && r > 0.0 ? ma++ : -1;
   }
   for (int j = 0; j < mP; ++j)

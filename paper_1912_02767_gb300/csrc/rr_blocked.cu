@@ -30,12 +30,13 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 // column in bar->fail; the block is then left as it is.  The inverse is
 // formed by forward substitution, one column per warp (lanes split each dot
 // product), into the upper triangle of the shared block (transposed).
-// Dynamic shared memory: kBlkSmem bytes.
+// Dynamic shared memory: potrf_block_smem(BLK) bytes.
+template <int BLK>
 __global__ void __launch_bounds__(1024) k_potrf_inv_block(double* G, int ldg, double* Linv, int ldl, int j0, int bb,
                                                           double piv_min, GridBar* bar) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  double (*A)[kBlk + 1] = (double (*)[kBlk + 1])smraw;
-  __shared__ double xd[kBlk];
+  double (*A)[BLK + 1] = (double (*)[BLK + 1])smraw;
+  __shared__ double xd[BLK];
   __shared__ int fail;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   if (*(volatile int*)&bar->fail || *(volatile int*)&bar->err) return;
@@ -87,21 +88,21 @@ __global__ void __launch_bounds__(1024) k_potrf_inv_block(double* G, int ldg, do
   // -L_ik x_k (lane-parallel FMAs, no reductions -- an FP64 warp instruction
   // costs the SM's FP64 pipe tens of cycles).  X[i][j] is kept at A[j][i].
   for (int j = wid; j < bb; j += nw) {
-    double acc[kBlk / 32];  // running sums of the rows this lane owns: rows i = lane + 32 q
+    double acc[BLK / 32];  // running sums of the rows this lane owns: rows i = lane + 32 q
 #pragma unroll
-    for (int q = 0; q < kBlk / 32; ++q) acc[q] = 0.0;
+    for (int q = 0; q < BLK / 32; ++q) acc[q] = 0.0;
     for (int k = j; k < bb; ++k) {
       // x_k = (delta_jk - sum_{j <= l < k} L_kl x_l) / L_kk, held by the lane owning row k
       double xk = 0.0;
       double ak = 0.0;
 #pragma unroll
-      for (int q = 0; q < kBlk / 32; ++q)  // register select, no local-memory indexing
+      for (int q = 0; q < BLK / 32; ++q)  // register select, no local-memory indexing
         if (q == (k >> 5)) ak = acc[q];
       if (lane == (k & 31)) xk = ((k == j ? 1.0 : 0.0) - ak) * xd[k];
       xk = __shfl_sync(0xffffffffu, xk, k & 31);
       if (lane == 0) A[j][k] = xk;  // diagonal entry too (overwritten with xd below)
 #pragma unroll
-      for (int q = 0; q < kBlk / 32; ++q) {
+      for (int q = 0; q < BLK / 32; ++q) {
         const int i = lane + 32 * q;
         if (i > k && i < bb) acc[q] += A[i][k] * xk;
       }
@@ -113,6 +114,9 @@ __global__ void __launch_bounds__(1024) k_potrf_inv_block(double* G, int ldg, do
     Linv[(size_t)(j0 + i) + (size_t)(j0 + j) * ldl] = i > j ? A[j][i] : (i == j ? xd[i] : 0.0);
   }
 }
+
+template __global__ void k_potrf_inv_block<64>(double*, int, double*, int, int, int, double, GridBar*);
+template __global__ void k_potrf_inv_block<128>(double*, int, double*, int, int, int, double, GridBar*);
 
 // V (p x nref, ld p): column k = the Householder vector of reflector k
 // (zero above row k+1, one at row k+1, below it the vector stored in

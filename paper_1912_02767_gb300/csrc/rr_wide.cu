@@ -22,6 +22,7 @@
 #include "kernels.h"
 #include "tri_common.cuh"
 #include "gridbar.cuh"
+#include <cooperative_groups.h>
 
 namespace sdpg {
 using namespace tri;
@@ -538,6 +539,224 @@ __global__ void __launch_bounds__(256) k_trid_backtr(const T* A, double* vb, int
   __syncthreads();
   for (int j = 0; j < nq; ++j)
     for (int i = tid; i < p; i += nt) Yb[(size_t)j * p + i] = (double)Ys[(size_t)j * p + i];
+}
+
+// Householder tridiagonalization of the symmetric H (p x p, ld p, FP64) on
+// ONE thread-block cluster of CL CTAs, the matrix held in the cluster's
+// distributed shared memory: CTA `rank` owns the columns c = rank + CL j
+// (full columns, ld p | 1).  Per column k of the reduction (Algorithm 2's
+// eigenproblem of H, reduced as in Golub & Van Loan 8.3.1):
+//   (a) the owner of column k forms the reflector P = I - t v v^T mapping
+//       H[k+1:, k] to beta e_1 and publishes v, t in its shared memory;
+//   -- cluster barrier --
+//   (b) every CTA copies v (distributed shared memory reads) and forms
+//       w_c = t H22[:, c] . v on its owned trailing columns (symmetric:
+//       column = row), split over row segments so that every FP64 lane does
+//       useful work (no warp reductions), and its share of w^T v;
+//   -- cluster barrier --
+//   (c) every CTA gathers w and the shares, w' = w - (t/2)(w^T v) v, and
+//       updates its owned columns, H22[:, c] -= v w'_c + w' v_c.
+// The step's buffers alternate by parity of k, so two cluster barriers per
+// column order every remote read before the next overwrite.  The owned
+// columns (Householder vectors below the subdiagonal, the last 2 x 2 block)
+// are written to A (p x p, ld p) at the end, (d, e, tau) to `vb` by each
+// step's owner, and CTA 0 runs the tail (scaling of (d, e)).
+// Dynamic shared memory: trid_cluster_smem(p, CL) bytes.
+template <int CL>
+__global__ void __launch_bounds__(kTridClThreads) k_trid_cluster(const double* __restrict__ H, double* A, int p,
+                                                                 int keep, double* vb, GridBar* b) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int ldl = p | 1, ncl = (p + CL - 1) / CL;
+  double* Al = (double*)smraw;            // ncl x ldl: owned column c = rank + CL jl at jl
+  double* vbuf = Al + (size_t)ncl * ldl;  // 2 x p: the step's reflector (owner), by parity of k
+  double* wbuf = vbuf + 2 * p;            // 2 x p: w_c at index c for the owned c
+  double* vloc = wbuf + 2 * p;            // p: local copy of v
+  double* wl = vloc + p;                  // p: gathered w, then w'
+  double* scb = wl + p;                   // 2 x 4: beta, t, scale, this CTA's share of w^T v
+  double* part = scb + 8;                 // kTridClThreads: segment partial sums
+  double* red = part + kTridClThreads;    // 32: block reductions
+  __shared__ double s_K;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  WideVec<double> V(vb, p, keep);
+  if (bar_failed(b)) return;  // the record is not written while this kernel runs: uniform
+  for (int jl = 0; jl < ncl; ++jl) {
+    const int c = rank + CL * jl;
+    if (c >= p) break;
+    for (int i = tid; i < p; i += nt)
+      Al[(size_t)jl * ldl + i] = 0.5 * (H[(size_t)c * p + i] + H[(size_t)i * p + c]);
+  }
+  cl.sync();  // every CTA of the cluster resident before the first remote access
+  for (int k = 0; k + 2 < p; ++k) {
+    const int r = p - k - 1, par = k & 1, o = k % CL;
+    double* vb_ = vbuf + par * p;
+    double* wb_ = wbuf + par * p;
+    double* sc_ = scb + par * 4;
+    if (o == rank) {  // (a)
+      double* colk = Al + (size_t)(k / CL) * ldl + (k + 1);
+      double s = 0;
+      for (int i = 1 + tid; i < r; i += nt) s += colk[i] * colk[i];
+      s = block_sum(s, red);
+      if (tid == 0) {
+        const double x0 = colk[0];
+        double beta = x0, t = 0, scale = 0;
+        if (s > 0.0) {
+          const double alpha = sqrt(x0 * x0 + s);
+          beta = x0 >= 0.0 ? -alpha : alpha;
+          t = (beta - x0) / beta;
+          scale = 1.0 / (x0 - beta);
+        }
+        sc_[0] = beta;
+        sc_[1] = t;
+        sc_[2] = scale;
+        V.d[k] = colk[-1];
+        V.e[k] = beta;
+        V.tau[k] = t;
+      }
+      __syncthreads();
+      const double scale = sc_[2];
+      for (int i = tid; i < r; i += nt) {
+        const double v = i == 0 ? 1.0 : colk[i] * scale;
+        vb_[i] = v;
+        if (i > 0) colk[i] = v;  // kept below the subdiagonal for the back-transform
+      }
+    }
+    cl.sync();  // reflector k published
+    const double* rv = cl.map_shared_rank(vb_, o);
+    const double t = *cl.map_shared_rank(sc_ + 1, o);  // the same value in every CTA
+    for (int i = tid; i < r; i += nt) vloc[i] = rv[i];
+    const int cf = k + 1 + ((rank - (k + 1)) % CL + CL) % CL;  // first owned trailing column
+    const int nc = cf < p ? (p - 1 - cf) / CL + 1 : 0;
+    __syncthreads();
+    if (t != 0.0 && nc > 0) {  // (b), uniform in the CTA
+      const int nseg = max(1, min(64, nt / nc));
+      for (int q = tid; q < nc * nseg; q += nt) {
+        const int a = q / nseg, g = q % nseg;
+        const double* col = Al + (size_t)((cf + a * CL) / CL) * ldl + (k + 1);
+        double acc = 0;
+        for (int i = g; i < r; i += nseg) acc += col[i] * vloc[i];
+        part[q] = acc;
+      }
+      __syncthreads();
+      double pk = 0;
+      for (int a = tid; a < nc; a += nt) {
+        double w = 0;
+        for (int g = 0; g < nseg; ++g) w += part[a * nseg + g];
+        w *= t;
+        const int c = cf + a * CL;
+        wb_[c] = w;
+        pk += w * vloc[c - k - 1];
+      }
+      pk = block_sum(pk, red);
+      if (tid == 0) sc_[3] = pk;
+    } else if (tid == 0) {
+      sc_[3] = 0.0;
+    }
+    cl.sync();  // w entries and shares published
+    if (t != 0.0) {  // (c), uniform in the cluster
+      for (int i = tid; i < r; i += nt) {
+        const int g = k + 1 + i;
+        wl[i] = *cl.map_shared_rank(wb_ + g, g % CL);
+      }
+      if (tid == 0) {
+        double kk = 0;
+        for (int o2 = 0; o2 < CL; ++o2) kk += *cl.map_shared_rank(sc_ + 3, o2);  // fixed order
+        s_K = 0.5 * t * kk;
+      }
+      __syncthreads();
+      const double K = s_K;
+      for (int i = tid; i < r; i += nt) wl[i] -= K * vloc[i];
+      __syncthreads();
+      for (int a = wid; a < nc; a += nw) {
+        const int c = cf + a * CL, jc = c - k - 1;
+        double* col = Al + (size_t)(c / CL) * ldl + (k + 1);
+        const double vc = vloc[jc], wc = wl[jc];
+        for (int i = lane; i < r; i += 32) col[i] -= vloc[i] * wc + wl[i] * vc;
+      }
+      __syncthreads();
+    }
+  }
+  for (int jl = 0; jl < ncl; ++jl) {
+    const int c = rank + CL * jl;
+    if (c >= p) break;
+    for (int i = tid; i < p; i += nt) A[(size_t)c * p + i] = Al[(size_t)jl * ldl + i];
+  }
+  __threadfence();
+  cl.sync();  // A and (d, e, tau) complete; no remote access after this point
+  if (rank != 0) return;
+  trid_tail(A, p, V, b);
+}
+
+// Largest p whose owned columns fit one CTA of a CL-CTA cluster.
+int trid_cluster_max_p(int cl) {
+  int p = 3;
+  while (trid_cluster_smem(p + 1, cl) <= kTridClSmemMax) ++p;
+  return p;
+}
+
+template <int CL>
+static int trid_cluster_ready() {
+  static int ok = -1;
+  if (ok >= 0) return ok;
+  ok = 0;
+  auto k = k_trid_cluster<CL>;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTridClSmemMax) != cudaSuccess ||
+      (CL > 8 && cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
+    cudaGetLastError();
+    return ok;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  cfg.gridDim = dim3(CL);
+  cfg.blockDim = dim3(kTridClThreads);
+  cfg.dynamicSmemBytes = kTridClSmemMax;
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int nclu = 0;
+  if (cudaOccupancyMaxActiveClusters(&nclu, k, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return ok;
+  }
+  ok = nclu > 0 ? 1 : 0;
+  return ok;
+}
+
+// Cluster width for a reduction of width p: 16 CTAs where the GPU schedules
+// such clusters, else 8; 0 when p exceeds what the cluster's shared memory
+// holds.
+int trid_cluster_width(int p) {
+  static int m16 = -1, m8 = -1;
+  if (m8 < 0) {
+    m16 = trid_cluster_ready<16>() ? trid_cluster_max_p(16) : 0;
+    m8 = trid_cluster_ready<8>() ? trid_cluster_max_p(8) : 0;
+  }
+  if (p <= m16) return 16;
+  if (p <= m8) return 8;
+  return 0;
+}
+
+int trid_cluster(cudaStream_t s, int cl, const double* H, double* A, int p, int keep, double* vb, GridBar* b) {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  cfg.gridDim = dim3(cl);
+  cfg.blockDim = dim3(kTridClThreads);
+  cfg.dynamicSmemBytes = trid_cluster_smem(p, cl);
+  cfg.stream = s;
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cl;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaError_t e = cl == 16 ? cudaLaunchKernelEx(&cfg, k_trid_cluster<16>, H, A, p, keep, vb, b)
+                           : cudaLaunchKernelEx(&cfg, k_trid_cluster<8>, H, A, p, keep, vb, b);
+  return e == cudaSuccess ? 0 : -1;
 }
 
 template __global__ void k_trid_coop<float>(const double*, float*, int, int, double*, GridBar*);

@@ -29,7 +29,7 @@ class Settings(C.Structure):
                 ("precision", C.c_int), ("exact_only", C.c_int), ("tol_coef", C.c_double),
                 ("tol_exp", C.c_double), ("expand_frac", C.c_double), ("mode_frac", C.c_double),
                 ("seed", C.c_ulonglong), ("rr_method", C.c_int), ("rr_fp32", C.c_int), ("proj_neg", C.c_int),
-                ("exact_solver", C.c_int)]
+                ("exact_solver", C.c_int), ("soft_lock", C.c_int)]
 
 
 class Info(C.Structure):
