@@ -50,6 +50,13 @@ def parse():
     ap.add_argument("--serve-maxcut-n", type=int, default=2000, help="serve: largest max-cut request n")
     ap.add_argument("--serve-theta-n", type=int, default=1000, help="serve: largest theta request n")
     ap.add_argument("--both-precisions", action="store_true", help="theta500: run the FP64 path too")
+    ap.add_argument("--soft-lock", type=int, default=0, choices=[0, 1],
+                    help="batch/serve: soft locking in LOBPCG (the batched run and its comparators alike)")
+    ap.add_argument("--batch-seconds", type=float, default=0.0,
+                    help="batch: stop the batched run after this wall time (0: run to completion)")
+    ap.add_argument("--alone-seconds", type=float, default=0.0,
+                    help="batch: wall-time limit of each one-at-a-time comparator set (0: none)")
+    ap.add_argument("--step-iters", type=int, default=100, help="batch: ADMM iterations per server step")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="theta500/maxcut64: one more solve capped at this many iterations with the per-kernel "
                          "event timers on; reports wall time against summed kernel time and the top kernels")
@@ -501,6 +508,10 @@ def run_admm(args):
                          "n_lobpcg": r["n_lobpcg"], "n_exact": r["n_exact"], "lobpcg_steps": r["lobpcg_steps"],
                          "device_ms_by_family": _family_ms(sdpgpu, c.solve)}
         out["oracle_exact_cpu"] = {"solves_per_s": 1.0 / t_or, "iters": ref["iters"], "obj": ref["obj"], "cores": 1}
+        if args.profile_iters > 0:
+            out["profile"] = profile_solve(sdpgpu, stream, inst, args.profile_iters,
+                                           dict(precision=P64, eps_abs=1e-4, rr_method=args.rr))
+            print("profile: %s" % json.dumps(out["profile"]), file=sys.stderr, flush=True)
     elif args.workload == "theta500":
         inst = gen.workload_theta500(0)
         gold = None
@@ -548,39 +559,77 @@ def run_admm(args):
                                                 if isinstance(v, dict) and "obj" in v}
     elif args.workload == "batch":
         insts = gen.workload_batch(args.count)
-        ctxs = [_ctx_for(sdpgpu, i, stream, PMX, eps_abs=1e-4, rr_method=args.rr) for i in insts]
-        t0 = time.perf_counter()
-        infos = sdpgpu.batch_solve(ctxs)
-        dt = time.perf_counter() - t0
-        out["mixed_batched"] = {"solves_per_s": len(insts) / dt, "s": dt,
-                                "statuses": {k: sum(1 for i in infos if i["status_name"] == k)
-                                             for k in set(i["status_name"] for i in infos)},
-                                "iters_max": max(i["iters"] for i in infos)}
-        out["mixed_batched"]["n_ladder_total"] = sum(i.get("n_ladder", 0) for i in infos)
+        kwb = dict(eps_abs=1e-4, rr_method=args.rr, soft_lock=args.soft_lock)
+
+        def drive(cs, slots, limit, label):
+            """Every context submitted at t = 0 to the continuous-batching
+            server (`slots` advanced together per step), stepped until all
+            finish or `limit` seconds pass (0: no limit)."""
+            srv = sdpgpu.Server(budget_bytes=200 << 30, max_slots=slots, iters_per_step=args.step_iters,
+                                stream=stream, **kwb)
+            tk = [srv.submit(c) for c in cs]
+            fin = {}
+            t0 = time.perf_counter()
+            nstep = 0
+            while len(fin) < len(cs):
+                a, q = srv.step()
+                nstep += 1
+                for j, t in enumerate(tk):
+                    if j not in fin:
+                        rc, info = srv.poll(t)
+                        if rc not in (sdpgpu.SDP_RUNNING, sdpgpu.SDP_QUEUED):
+                            fin[j] = (time.perf_counter() - t0, info)
+                if nstep % 10 == 0:
+                    print("%s t=%.1fs active=%d queued=%d done=%d" % (label, time.perf_counter() - t0, a, q, len(fin)),
+                          file=sys.stderr, flush=True)
+                if a == 0 and q == 0:
+                    break
+                if limit > 0 and time.perf_counter() - t0 > limit:
+                    break
+            wall = time.perf_counter() - t0
+            srv.close()
+            return fin, wall
+
+        ctxs = [_ctx_for(sdpgpu, i, stream, PMX, **kwb) for i in insts]
+        fin, wall = drive(ctxs, len(ctxs), args.batch_seconds, "batched")
+        infos = {j: v[1] for j, v in fin.items()}
+        out["mixed_batched"] = {"completed": len(fin), "instances": len(insts), "s": wall,
+                                "solves_per_s": len(fin) / wall, "time_limit_s": args.batch_seconds or None,
+                                "statuses": {k: sum(1 for i in infos.values() if i["status_name"] == k)
+                                             for k in set(i["status_name"] for i in infos.values())},
+                                "iters_max": max((i["iters"] for i in infos.values()), default=0),
+                                "completed_n": sorted(insts[j].n for j in fin)}
         print("batched: %s" % json.dumps(out["mixed_batched"]), file=sys.stderr, flush=True)
         # one at a time on a stratified subset (quartile midpoints in n), the
-        # same mixed path and the plain FP64 path: throughput estimates of
-        # one-solve-at-a-time on this size distribution
+        # same mixed path and the plain FP64 path, each set within its own
+        # time limit: throughput estimates of one-solve-at-a-time
         order = sorted(range(len(insts)), key=lambda q: insts[q].n)
         sub = sorted(set(order[min(len(order) - 1, int((j + 0.5) * len(order) / 4))] for j in range(4)))
         for name, prec in [("mixed_one_at_a_time", PMX), ("fp64_one_at_a_time", P64)]:
-            cs1 = [_ctx_for(sdpgpu, insts[q], stream, prec, eps_abs=1e-4, rr_method=args.rr) for q in sub]
-            t0 = time.perf_counter()
-            rs = [c.solve() for c in cs1]
-            dt1 = time.perf_counter() - t0
-            out[name] = {"solves_per_s": len(sub) / dt1, "instances_n": [insts[q].n for q in sub],
-                         "statuses": [r["status_name"] for r in rs], "iters": [r["iters"] for r in rs],
-                         "same_as_batched": [abs(r["obj"] - infos[q]["obj"]) <= 1e-9 * abs(r["obj"])
-                                             and r["iters"] == infos[q]["iters"] for r, q in zip(rs, sub)],
-                         "rel_obj_vs_batched": [abs(r["obj"] - infos[q]["obj"]) / abs(r["obj"]) for r, q in
-                                                zip(rs, sub)]}
+            cs1 = [_ctx_for(sdpgpu, insts[q], stream, prec, **kwb) for q in sub]
+            done1, t_all = {}, 0.0
+            for j, c in enumerate(cs1):
+                f1, w1 = drive([c], 1, max(1.0, args.alone_seconds - t_all), name)
+                t_all += w1
+                if f1:
+                    done1[j] = f1[0][1]
+                if args.alone_seconds > 0 and t_all >= args.alone_seconds:
+                    break
+            out[name] = {"completed": len(done1), "tried": len(sub), "s": t_all,
+                         "solves_per_s": len(done1) / t_all if t_all > 0 else None,
+                         "instances_n": [insts[sub[j]].n for j in done1],
+                         "statuses": [r["status_name"] for r in done1.values()],
+                         "iters": [r["iters"] for r in done1.values()],
+                         "same_as_batched": [sub[j] in infos and abs(r["obj"] - infos[sub[j]]["obj"]) <= 1e-9 * abs(r["obj"])
+                                             and r["iters"] == infos[sub[j]]["iters"] for j, r in done1.items()]}
             print("%s: %s" % (name, json.dumps(out[name])), file=sys.stderr, flush=True)
-        out["batched_vs_fp64_one_at_a_time"] = (out["mixed_batched"]["solves_per_s"] /
-                                                out["fp64_one_at_a_time"]["solves_per_s"])
+        a1, b1 = out["mixed_batched"]["solves_per_s"], out["fp64_one_at_a_time"]["solves_per_s"]
+        out["batched_vs_fp64_one_at_a_time"] = a1 / b1 if b1 else None
         out["n_range"] = [min(i.n for i in insts), max(i.n for i in insts)]
+        out["soft_lock"] = args.soft_lock
     elif args.workload == "serve":
         reqs = gen.workload_serving(args.count, maxcut_n=(100, args.serve_maxcut_n), theta_n=(100, args.serve_theta_n))
-        kw = dict(eps_abs=1e-4, tol_coef=0.1, precision=PMX)
+        kw = dict(eps_abs=1e-4, tol_coef=0.1, precision=PMX, soft_lock=args.soft_lock)
         srv = sdpgpu.Server(budget_bytes=64 << 30, max_slots=32, iters_per_step=100, stream=stream, **kw)
         ctxs, tickets, arrive, done_t = {}, {}, {}, {}
         t0 = time.perf_counter()
@@ -627,7 +676,8 @@ def run_admm(args):
                     "p99_s": float(np.percentile(lat, 99)) if len(lat) else None, "statuses": st,
                     "infeasible_detected": pinf_ok,
                     "infeasible_total": sum(1 for r in reqs if r[1].meta.get("family") == "pinf"),
-                    "arrival_rate_per_s": 50.0, "wall_s": wall})
+                    "arrival_rate_per_s": 50.0, "wall_s": wall, "soft_lock": args.soft_lock,
+                    "sizes": {"maxcut_n_max": args.serve_maxcut_n, "theta_n_max": args.serve_theta_n}})
     print(json.dumps(out), flush=True)
 
 

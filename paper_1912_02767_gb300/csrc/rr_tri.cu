@@ -73,30 +73,26 @@ __global__ void __launch_bounds__(1024) k_rr_tri(Inst* insts, const int* list, i
   }
   if (tid == 0) s_fail = 0;
   __syncthreads();
+  // pivot reciprocals (in `sig`, free until the shifts): each one computed
+  // once, by the lane that finishes that pivot -- an FP64 division costs an
+  // SM sub-partition about twelve FP64 issue slots, whatever the lanes
+  T* rcp = sig;
+  if (tid == 0) rcp[0] = (T)1 / B[0];
+  __syncthreads();
   for (int j = 0; j < p; ++j) {
     const T djj = B[j + j * ldp];
     if (!(djj > piv)) {
       if (tid == 0) s_fail = j + 1;
       break;  // every thread reads the same pivot: uniform exit
     }
-    // scalar work only in the warps that use it, one lane each (an SM
-    // issues about two FP64 operations per clock: a division in every
-    // thread of the block would cost more than the update itself)
-    if (j + 1 + wid < p) {
-      T inv = (T)0;
-      if (lane == 0) inv = (T)1 / djj;
-      inv = __shfl_sync(0xffffffffu, inv, 0);
-      for (int c = j + 1 + wid; c < p; c += nw) {
-        const T bc = B[c + j * ldp] * inv;
-        for (int r = c + lane; r < p; r += 32) B[r + c * ldp] -= B[r + j * ldp] * bc;
-      }
+    const T inv = rcp[j];
+    for (int c = j + 1 + wid; c < p; c += nw) {
+      const T bc = B[c + j * ldp] * inv;
+      for (int r = c + lane; r < p; r += 32) B[r + c * ldp] -= B[r + j * ldp] * bc;
+      if (c == j + 1 && lane == 0) rcp[c] = (T)1 / B[c + c * ldp];  // the next pivot is final now
     }
-    if (j > 0 && j + (tid & ~31) < p) {  // column j-1 is no longer read: scale it to L~
-      T invp = (T)0;
-      if (lane == 0) invp = (T)1 / B[(j - 1) + (j - 1) * ldp];
-      invp = __shfl_sync(0xffffffffu, invp, 0);
-      for (int r = j + tid; r < p; r += nt) B[r + (j - 1) * ldp] *= invp;
-    }
+    if (j > 0)  // column j-1 is no longer read: scale it to L~
+      for (int r = j + tid; r < p; r += nt) B[r + (j - 1) * ldp] *= rcp[j - 1];
     __syncthreads();
   }
   __syncthreads();
@@ -194,7 +190,7 @@ __global__ void __launch_bounds__(1024) k_rr_tri(Inst* insts, const int* list, i
       }
     }
     __syncthreads();
-    {
+    if (wid * 32 < r) {  // warps holding rows of w
       T pw = 0;
       if (tid < r) {
         T acc = 0;
@@ -205,12 +201,19 @@ __global__ void __launch_bounds__(1024) k_rr_tri(Inst* insts, const int* list, i
       }
       pw = warp_sum(pw);
       if (lane == 0) s_red[wid] = pw;
+    } else if (lane == 0) {
+      s_red[wid] = (T)0;
     }
     __syncthreads();
-    // A22 -= v w'^T + w' v^T with w' = w - K v, K = t/2 w^T v
-    if (wid < r) {
+    if (wid == 0) {  // K = t/2 w^T v, once
       T K = lane < nw ? s_red[lane] : (T)0;
       K = warp_sum(K) * ((T)0.5 * t);
+      if (lane == 0) s_sc[0] = K;
+    }
+    __syncthreads();
+    // A22 -= v w'^T + w' v^T with w' = w - K v
+    if (wid < r) {
+      const T K = s_sc[0];
       for (int c = wid; c < r; c += nw) {
         const T vc = vv[c], wc = wv[c] - K * vc;
         T* col = B + (size_t)(k + 1 + c) * ldp + (k + 1);
@@ -290,8 +293,20 @@ __global__ void __launch_bounds__(1024) k_rr_tri(Inst* insts, const int* list, i
                           false);
     if (dbl) {
       __syncthreads();
-      int S4 = 4;
-      while (S4 > 1 && S4 * keep > nt) S4 >>= 1;
+      // lanes per eigenvalue for the FP64 refinement (about 33 bits from
+      // the FP32 bracket): every count is one FP64 chain, and warps sharing
+      // an SM sub-partition share its FP64 issue, so take the S that needs
+      // the fewest chains per sub-partition, ceil(warps / 4) * 33 / log2(S + 1)
+      int S4 = 1;
+      float best = 3.0e38f;
+      for (int S = 1; S <= 32 && S * keep <= nt; S <<= 1) {
+        const int W = (S * keep + 31) / 32;
+        const float cost = (float)((W + 3) / 4) * (33.0f / log2f((float)S + 1.0f));
+        if (cost < best * 0.999f) {
+          best = cost;
+          S4 = S;
+        }
+      }
       section_search<T>(d, e2, p, keep, S4, tid / S4, nt / S4, (T)4 * K<T>::eps, (T)(64.0f * K<float>::eps),
                         (T)0, (T)K<T>::safmin, lam, true);
     }
@@ -317,10 +332,23 @@ __global__ void __launch_bounds__(1024) k_rr_tri(Inst* insts, const int* list, i
   for (int q = tid; q < keep; q += nt) inv_iter<T, T>(d, e, p, sig[q], Z + q, (size_t)keep, WS + q, (size_t)keep, q);
   __syncthreads();
 
-  // ---- 7. classical Gram-Schmidt, twice, over the keep vectors
+  // ---- 7. classical Gram-Schmidt, twice, within each cluster of close
+  // eigenvalues (gaps at most 1e-3 of the unit-scaled T, the criterion of
+  // LAPACK's stein): inverse-iteration vectors of eigenvalues farther apart
+  // are orthogonal to about eps / gap already.  FP32 (the comparison path):
+  // over all the vectors.
+  int* cst = (int*)lcol;  // first vector of the cluster of q (lcol is free until step 9)
+  if (tid == 0) {
+    cst[0] = 0;
+    for (int q = 1; q < keep; ++q)
+      cst[q] = sizeof(T) == sizeof(double) && lam[q] - lam[q - 1] > (T)1e-3 ? q : (sizeof(T) == sizeof(double) ? cst[q - 1] : 0);
+  }
+  __syncthreads();
   for (int q = 1; q < keep; ++q) {
+    const int k0 = cst[q];
+    if (k0 == q) continue;  // uniform: a cluster of its own (the vector is unit-norm already)
     for (int pass = 0; pass < 2; ++pass) {
-      for (int k = wid; k < q; k += nw) {
+      for (int k = k0 + wid; k < q; k += nw) {
         T s = 0;
         for (int i = lane; i < p; i += 32) s += Z[(size_t)i * keep + k] * Z[(size_t)i * keep + q];
         s = warp_sum(s);
@@ -329,7 +357,7 @@ __global__ void __launch_bounds__(1024) k_rr_tri(Inst* insts, const int* list, i
       __syncthreads();
       for (int i = tid; i < p; i += nt) {
         T acc = Z[(size_t)i * keep + q];
-        for (int k = 0; k < q; ++k) acc -= part[k] * Z[(size_t)i * keep + k];
+        for (int k = k0; k < q; ++k) acc -= part[k] * Z[(size_t)i * keep + k];
         Z[(size_t)i * keep + q] = acc;
       }
       __syncthreads();

@@ -60,6 +60,53 @@ __device__ __forceinline__ int sturm_below(const T* d, const T* e2, int p, T x, 
   return c;
 }
 
+// Number of eigenvalues of the tridiagonal (d, e2 = e^2) below x by the signs
+// of its leading principal minors f_i = det(T_i - x I): f_0 = 1, f_1 = d_0 - x,
+// f_{i+1} = (d_i - x) f_i - e_{i-1}^2 f_{i-1}; the count is the number of sign
+// changes along f_0 .. f_p, a zero minor taking the sign opposite to its
+// predecessor (the Sturm property of the minors; Wilkinson, The Algebraic
+// Eigenvalue Problem, 5.37).  A subtraction, a multiplication and an FMA per
+// row and no division: on GB300 an FP64 division costs an SM sub-partition
+// about twelve FP64 issue slots, and a Sturm count is one dependent chain.
+// The pair (f_{i-1}, f_i) is rescaled by a power of two (integer exponent
+// arithmetic) whenever the larger leaves [2^-600, 2^600]; for a matrix scaled
+// to unit norm and |x| <= 1.01 a row grows the pair at most threefold.
+__device__ __forceinline__ int sturm_below_minors(const double* __restrict__ d, const double* __restrict__ e2, int p,
+                                                  double x) {
+  double fa = 1.0, fb = d[0] - x;
+  int sa = 0, c = 0;  // sign of f_{i}: 0 positive, 1 negative (f_0 = 1)
+  for (int i = 0;; ++i) {
+    const long long bb = __double_as_longlong(fb);
+    const int sb = ((unsigned long long)bb << 1) == 0 ? 1 - sa : (int)((unsigned long long)bb >> 63);
+    c += sb != sa;
+    sa = sb;
+    if (i + 1 >= p) break;
+    const int exb = (int)((bb >> 52) & 0x7ff), exa = (int)((__double_as_longlong(fa) >> 52) & 0x7ff);
+    const int ex = exa > exb ? exa : exb;
+    if (ex > 1023 + 600 || ex < 1023 - 600) {
+      if (ex < 2047 && ex > 0) {  // not inf / nan / both zero
+        const double sc = __longlong_as_double((long long)(2046 - ex) << 52);  // 2^(1023 - ex)
+        fa *= sc;
+        fb *= sc;
+      }
+    }
+    const double t = e2[i] * fa;
+    const double fn = fma(d[i + 1] - x, fb, -t);
+    fa = fb;
+    fb = fn;
+  }
+  return c;
+}
+
+template <typename T>
+__device__ __forceinline__ int count_below(const T* d, const T* e2, int p, T x, T pivmin) {
+  return sturm_below(d, e2, p, x, pivmin);
+}
+template <>
+__device__ __forceinline__ int count_below<double>(const double* d, const double* e2, int p, double x, double) {
+  return sturm_below_minors(d, e2, p, x);
+}
+
 // Start vector of inverse iteration: uniform in [-1, 1) from the Philox
 // stream keyed for this purpose (row i, vector q).
 template <typename T>
@@ -90,7 +137,7 @@ __device__ void section_search(const TS* d, const TS* e2, int p, int keep, int S
       const TS c = (TS)lam[q];
       lo = c - lo0;
       hi = c + lo0;
-      const int clo = sturm_below(d, e2, p, lo, pivmin), chi = sturm_below(d, e2, p, hi, pivmin);
+      const int clo = count_below(d, e2, p, lo, pivmin), chi = count_below(d, e2, p, hi, pivmin);
       if (!(clo <= J && J < chi)) {
         lo = (TS)-1.01;
         hi = (TS)1.01;
@@ -98,7 +145,7 @@ __device__ void section_search(const TS* d, const TS* e2, int p, int keep, int S
     }
     for (int it = 0; it < 200 && hi - lo > tol; ++it) {
       const TS step = (hi - lo) / (TS)(S + 1);
-      const int c = sturm_below(d, e2, p, lo + step * (TS)(sl + 1), pivmin);
+      const int c = count_below(d, e2, p, lo + step * (TS)(sl + 1), pivmin);
       unsigned b = __ballot_sync(gmask, c > J) >> gbase;
       if (S < 32) b &= (1u << S) - 1u;
       const int f = __ffs(b) - 1;  // first point above eigenvalue J (-1: none)
@@ -112,45 +159,78 @@ __device__ void section_search(const TS* d, const TS* e2, int p, int keep, int S
   }
 }
 
+// Row-interchange flag of the factorization, kept in the lowest mantissa
+// bit of the stored multiplier (a change of at most one unit in its last
+// place).
+__device__ __forceinline__ double pack_flag(double f, int sw) {
+  return __longlong_as_double((__double_as_longlong(f) & ~1LL) | (long long)sw);
+}
+__device__ __forceinline__ float pack_flag(float f, int sw) { return __int_as_float((__float_as_int(f) & ~1) | sw); }
+__device__ __forceinline__ int flag_of(double f) { return (int)(__double_as_longlong(f) & 1LL); }
+__device__ __forceinline__ int flag_of(float f) { return __float_as_int(f) & 1; }
+
 // Inverse iteration for the eigenvector of the tridiagonal (d, e) nearest
-// the shift sg: three solves of (T - sg I) x = z by Gaussian elimination
-// with partial pivoting (U has two superdiagonals, a zero pivot becomes
-// tiny), from the Philox start vector of column q, normalized each time.
-// The vector lives at z[i * zs] (element type TZ), the factors at
-// w[(3 i + c) * ws], c = 0, 1, 2.
+// the shift sg: T - sg I = P L U is factored once by Gaussian elimination
+// with partial pivoting (U has two superdiagonals; a zero pivot becomes
+// tiny), then three solves (T - sg I) x = z from the Philox start vector of
+// column q, normalized each time.  One reciprocal per row in the
+// factorization; the solves are multiplications only.  The vector lives at
+// z[i * zs] (element type TZ); per row i the factors are kept at
+// w[(3 i + c) * ws]: c = 0 the multiplier (row-interchange flag in its last
+// bit), 1 the reciprocal of the pivot u0, 2 the first superdiagonal u1 (the
+// second, u2, is e_{i+1} after an interchange and zero otherwise).
 template <typename T, typename TZ>
 __device__ void inv_iter(const T* __restrict__ d, const T* __restrict__ e, int p, T sg, TZ* __restrict__ z, size_t zs,
                          T* __restrict__ w, size_t ws, int q) {
   const T tiny = K<T>::eps;
+  T a = d[0] - sg, bc = p > 1 ? e[0] : (T)0;
+  for (int i = 0; i + 1 < p; ++i) {
+    const T ei = e[i], an = d[i + 1] - sg, en = i + 2 < p ? e[i + 1] : (T)0;
+    T f, r, u1;
+    int sw;
+    if (fabs(a) >= fabs(ei)) {  // pivot on the active row
+      if (a == (T)0) a = tiny;
+      r = (T)1 / a;
+      f = ei * r;
+      u1 = bc;
+      a = an - f * bc;
+      bc = en;
+      sw = 0;
+    } else {  // interchange with row i+1
+      r = (T)1 / ei;
+      f = a * r;
+      u1 = an;
+      a = bc - f * an;
+      bc = -f * en;
+      sw = 1;
+    }
+    T* wi = w + (size_t)3 * i * ws;
+    wi[0] = pack_flag(f, sw);
+    wi[ws] = r;
+    wi[2 * ws] = u1;
+  }
+  if (a == (T)0) a = tiny;
+  const T rlast = (T)1 / a;
   for (int i = 0; i < p; ++i) z[(size_t)i * zs] = (TZ)start_value<T>(i, q);
   for (int it = 0; it < 3; ++it) {
-    T a = d[0] - sg, bc = p > 1 ? e[0] : (T)0, zi = (T)z[0];
-    for (int i = 0; i + 1 < p; ++i) {
-      const T ei = e[i], an = d[i + 1] - sg, en = i + 2 < p ? e[i + 1] : (T)0;
+    T zi = (T)z[0];
+    for (int i = 0; i + 1 < p; ++i) {  // z <- L^{-1} P z
+      const T fp = w[(size_t)3 * i * ws];
       const T zn = (T)z[(size_t)(i + 1) * zs];
-      T u0, u1, u2, zr;
-      if (fabs(a) >= fabs(ei)) {  // pivot on the active row
-        if (a == (T)0) a = tiny;
-        const T f = ei / a;
-        u0 = a; u1 = bc; u2 = 0; zr = zi;
-        a = an - f * bc; bc = en; zi = zn - f * zi;
-      } else {  // interchange with row i+1
-        const T f = a / ei;
-        u0 = ei; u1 = an; u2 = en; zr = zn;
-        a = bc - f * an; bc = -f * en; zi = zi - f * zn;
+      if (flag_of(fp)) {
+        z[(size_t)i * zs] = (TZ)zn;
+        zi = zi - fp * zn;
+      } else {
+        z[(size_t)i * zs] = (TZ)zi;
+        zi = zn - fp * zi;
       }
-      T* wi = w + (size_t)3 * i * ws;
-      wi[0] = u0;
-      wi[ws] = u1;
-      wi[2 * ws] = u2;
-      z[(size_t)i * zs] = (TZ)zr;
     }
-    if (a == (T)0) a = tiny;
-    T x1 = zi / a, x2 = 0, mx = fabs(x1);
+    T x1 = zi * rlast, x2 = 0, mx = fabs(x1);
     z[(size_t)(p - 1) * zs] = (TZ)x1;
-    for (int i = p - 2; i >= 0; --i) {
+    for (int i = p - 2; i >= 0; --i) {  // U x = z
       const T* wi = w + (size_t)3 * i * ws;
-      const T xi = ((T)z[(size_t)i * zs] - wi[ws] * x1 - wi[2 * ws] * x2) / wi[0];
+      const T u2 = flag_of(wi[0]) && i + 2 < p ? e[i + 1] : (T)0;
+      const T xi = ((T)z[(size_t)i * zs] - wi[2 * ws] * x1 - u2 * x2) * wi[ws];
       z[(size_t)i * zs] = (TZ)xi;
       x2 = x1;
       x1 = xi;
