@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--alone-seconds", type=float, default=0.0,
                     help="batch: wall-time limit of each one-at-a-time comparator set (0: none)")
     ap.add_argument("--step-iters", type=int, default=100, help="batch: ADMM iterations per server step")
+    ap.add_argument("--batch-n-max", type=int, default=1024, help="batch: largest instance n (smallest 64)")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="theta500/maxcut64: one more solve capped at this many iterations with the per-kernel "
                          "event timers on; reports wall time against summed kernel time and the top kernels")
@@ -558,7 +559,7 @@ def run_admm(args):
             out["rel_obj_vs_tightest_exact"] = {k: abs(v["obj"] - ref) / abs(ref) for k, v in out.items()
                                                 if isinstance(v, dict) and "obj" in v}
     elif args.workload == "batch":
-        insts = gen.workload_batch(args.count)
+        insts = gen.workload_batch(args.count, n_hi=args.batch_n_max)
         kwb = dict(eps_abs=1e-4, rr_method=args.rr, soft_lock=args.soft_lock)
 
         def drive(cs, slots, limit, label):

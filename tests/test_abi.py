@@ -86,3 +86,5 @@ def test_default_rayleigh_ritz_settings(lib):
     from paper_1912_02767_gb300 import sdpgpu
     s = sdpgpu.settings()
     assert s.rr_method == 0 and s.rr_fp32 == 0 and s.precision == sdpgpu.PREC_FP64
+    # Algorithm 3's full trial subspace span(X, R, dX) unless soft locking is asked for
+    assert s.soft_lock == 0 and s.proj_neg == 0 and s.exact_solver == 0

@@ -39,6 +39,21 @@ def test_projection_matches_closed_form_and_oracle(sdp, orc, n, f):
     assert np.linalg.norm(P - ref) <= np.sqrt(2) * info["res_fro"] + 1e-10 * nW
 
 
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+@pytest.mark.parametrize("n,f", [(300, 0.3), (1024, 0.1)])
+def test_projection_soft_locking(sdp, n, f, prec):
+    """Soft locking (converged pairs leave R and dX) narrows the trial
+    subspace but reaches the same projection; (1024, 0.1) runs the cluster
+    tridiagonalization (p about 300)."""
+    sp = gen.random_spectrum(n, f, np.random.default_rng(n + 7))
+    p = sdp.PREC_FP64 if prec == "fp64" else sdp.PREC_BF16X3
+    ctx = sdp.Context(precision=p, soft_lock=1)
+    P, V, info = ctx.project_psd(sp["W"], sp["X0"])
+    err = np.linalg.norm(P - closed_form(sp)) / np.linalg.norm(sp["W"])
+    assert err <= (TOL_FP64 if prec == "fp64" else 1e-4), err
+    assert info["npos"] == sp["k"]
+
+
 def test_projection_expands_block(sdp):
     """Start with 3 random columns for 12 positive eigenvalues: the block must
     grow by random columns (Algorithm 3, expansion) and still be exact."""
