@@ -65,7 +65,7 @@ __host__ __device__ inline size_t rr_tri_smem_bytes(int p, int zk, int tsize) {
 constexpr size_t kRRTriSmemMax = 231936;  // 227 KiB per CTA less the kernel's static shared memory
 // threads of a k_rr_tri CTA for widths up to p (p <= threads): fewer warps
 // per barrier for narrow subspaces, all 32 for wide ones
-constexpr int kRRTriMaxF64 = 1024;  // widest FP64 trial subspace on the one-CTA route (its shared memory decides below this)
+constexpr int kRRTriMaxF64 = 1024;  // cap on the FP64 width of the one-CTA route (shared memory binds first)
 inline int rr_tri_threads(int p) { return p <= 32 ? 128 : (p <= 64 ? 256 : (p <= 128 ? 512 : 1024)); }
 __global__ void k_resid(Inst* insts, WorkMap wm);
 __global__ void k_resid_finish(Inst* insts, const int* list, int last_allowed);
