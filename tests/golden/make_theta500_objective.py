@@ -2,8 +2,8 @@
 LOBPCG-ADMM (Algorithm 1 with the projection of Algorithm 3) objective on the
 Lovasz-theta workload n = 500, p = 0.2 (seeded), rho = 10, residual 1e-4 --
 the expected value of the GPU's mixed-precision solve of that workload.
-Calls only oracle/ and the seeded input generator.  Takes about an hour on
-one core.
+Calls only oracle/ and the seeded input generator.  Takes about twenty
+minutes on one core.
 
     python tests/golden/make_theta500_objective.py
 """
