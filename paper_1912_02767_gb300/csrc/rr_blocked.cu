@@ -115,8 +115,7 @@ __global__ void __launch_bounds__(1024) k_potrf_inv_block(double* G, int ldg, do
   }
 }
 
-template __global__ void k_potrf_inv_block<64>(double*, int, double*, int, int, int, double, GridBar*);
-template __global__ void k_potrf_inv_block<128>(double*, int, double*, int, int, int, double, GridBar*);
+template __global__ void k_potrf_inv_block<kPotrfBlk>(double*, int, double*, int, int, int, double, GridBar*);
 
 // V (p x nref, ld p): column k = the Householder vector of reflector k
 // (zero above row k+1, one at row k+1, below it the vector stored in
