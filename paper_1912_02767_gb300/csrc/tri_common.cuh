@@ -4,10 +4,51 @@
 // S-section search for selected eigenvalues (bisection on the Sturm count),
 // and inverse iteration by Gaussian elimination with partial pivoting.
 #pragma once
+#include <math.h>
+#include <string.h>
 #include "common.cuh"
 
 namespace sdpg {
 namespace tri {
+
+// Bit patterns of floating-point values (device: register moves; the host
+// forms serve the CPU tests of these helpers).
+__host__ __device__ __forceinline__ long long dbits(double x) {
+#ifdef __CUDA_ARCH__
+  return __double_as_longlong(x);
+#else
+  long long b;
+  memcpy(&b, &x, sizeof b);
+  return b;
+#endif
+}
+__host__ __device__ __forceinline__ double dfrom(long long b) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double(b);
+#else
+  double x;
+  memcpy(&x, &b, sizeof x);
+  return x;
+#endif
+}
+__host__ __device__ __forceinline__ int fbits(float x) {
+#ifdef __CUDA_ARCH__
+  return __float_as_int(x);
+#else
+  int b;
+  memcpy(&b, &x, sizeof b);
+  return b;
+#endif
+}
+__host__ __device__ __forceinline__ float ffrom(int b) {
+#ifdef __CUDA_ARCH__
+  return __int_as_float(b);
+#else
+  float x;
+  memcpy(&x, &b, sizeof x);
+  return x;
+#endif
+}
 
 template <typename T>
 struct K;
@@ -48,7 +89,7 @@ __device__ __forceinline__ T warp_max(T v) {
 // sequence).  A pivot smaller than pivmin in magnitude is replaced by
 // -pivmin, which keeps the count monotone in x.
 template <typename T>
-__device__ __forceinline__ int sturm_below(const T* d, const T* e2, int p, T x, T pivmin) {
+__host__ __device__ __forceinline__ int sturm_below(const T* d, const T* e2, int p, T x, T pivmin) {
   T q = d[0] - x;
   if (fabs(q) < pivmin) q = -pivmin;
   int c = q < (T)0;
@@ -63,29 +104,37 @@ __device__ __forceinline__ int sturm_below(const T* d, const T* e2, int p, T x, 
 // Number of eigenvalues of the tridiagonal (d, e2 = e^2) below x by the signs
 // of its leading principal minors f_i = det(T_i - x I): f_0 = 1, f_1 = d_0 - x,
 // f_{i+1} = (d_i - x) f_i - e_{i-1}^2 f_{i-1}; the count is the number of sign
-// changes along f_0 .. f_p, a zero minor taking the sign opposite to its
-// predecessor (the Sturm property of the minors; Wilkinson, The Algebraic
-// Eigenvalue Problem, 5.37).  A subtraction, a multiplication and an FMA per
+// changes along f_0 .. f_p (the Sturm property of the minors; Wilkinson, The
+// Algebraic Eigenvalue Problem, 5.37).  A minor that is exactly zero is
+// replaced by -2^-300 times its predecessor -- its pivot f_i / f_{i-1} taken
+// as tiny and negative, as the LDL^T count takes a zero pivot as -pivmin --
+// so it counts as a sign change and the recurrence goes on through it (two
+// zero minors in a row, as at an eigenvalue of a block split off by a zero
+// e_i, would otherwise zero every later one).  A subtraction, a multiplication and an FMA per
 // row and no division: on GB300 an FP64 division costs an SM sub-partition
 // about twelve FP64 issue slots, and a Sturm count is one dependent chain.
 // The pair (f_{i-1}, f_i) is rescaled by a power of two (integer exponent
 // arithmetic) whenever the larger leaves [2^-600, 2^600]; for a matrix scaled
 // to unit norm and |x| <= 1.01 a row grows the pair at most threefold.
-__device__ __forceinline__ int sturm_below_minors(const double* __restrict__ d, const double* __restrict__ e2, int p,
-                                                  double x) {
+__host__ __device__ __forceinline__ int sturm_below_minors(const double* __restrict__ d,
+                                                           const double* __restrict__ e2, int p, double x) {
   double fa = 1.0, fb = d[0] - x;
   int sa = 0, c = 0;  // sign of f_{i}: 0 positive, 1 negative (f_0 = 1)
   for (int i = 0;; ++i) {
-    const long long bb = __double_as_longlong(fb);
-    const int sb = ((unsigned long long)bb << 1) == 0 ? 1 - sa : (int)((unsigned long long)bb >> 63);
+    long long bb = dbits(fb);
+    if (((unsigned long long)bb << 1) == 0) {  // a zero minor
+      fb = -fa * 0x1p-300;
+      bb = dbits(fb);
+    }
+    const int sb = (int)((unsigned long long)bb >> 63);
     c += sb != sa;
     sa = sb;
     if (i + 1 >= p) break;
-    const int exb = (int)((bb >> 52) & 0x7ff), exa = (int)((__double_as_longlong(fa) >> 52) & 0x7ff);
+    const int exb = (int)((bb >> 52) & 0x7ff), exa = (int)((dbits(fa) >> 52) & 0x7ff);
     const int ex = exa > exb ? exa : exb;
     if (ex > 1023 + 600 || ex < 1023 - 600) {
       if (ex < 2047 && ex > 0) {  // not inf / nan / both zero
-        const double sc = __longlong_as_double((long long)(2046 - ex) << 52);  // 2^(1023 - ex)
+        const double sc = dfrom((long long)(2046 - ex) << 52);  // 2^(1023 - ex)
         fa *= sc;
         fb *= sc;
       }
@@ -99,18 +148,19 @@ __device__ __forceinline__ int sturm_below_minors(const double* __restrict__ d, 
 }
 
 template <typename T>
-__device__ __forceinline__ int count_below(const T* d, const T* e2, int p, T x, T pivmin) {
+__host__ __device__ __forceinline__ int count_below(const T* d, const T* e2, int p, T x, T pivmin) {
   return sturm_below(d, e2, p, x, pivmin);
 }
 template <>
-__device__ __forceinline__ int count_below<double>(const double* d, const double* e2, int p, double x, double) {
+__host__ __device__ __forceinline__ int count_below<double>(const double* d, const double* e2, int p, double x,
+                                                            double) {
   return sturm_below_minors(d, e2, p, x);
 }
 
 // Start vector of inverse iteration: uniform in [-1, 1) from the Philox
 // stream keyed for this purpose (row i, vector q).
 template <typename T>
-__device__ __forceinline__ T start_value(int i, int q) {
+__host__ __device__ __forceinline__ T start_value(int i, int q) {
   uint32_t c[4] = {(uint32_t)i, (uint32_t)q, 0x52525452u, 0u};
   philox4x32_10(c, 0x7452694Eu, 0x49544552u);
   return (T)((double)c[0] * (1.0 / 2147483648.0) - 1.0);
@@ -162,12 +212,12 @@ __device__ void section_search(const TS* d, const TS* e2, int p, int keep, int S
 // Row-interchange flag of the factorization, kept in the lowest mantissa
 // bit of the stored multiplier (a change of at most one unit in its last
 // place).
-__device__ __forceinline__ double pack_flag(double f, int sw) {
-  return __longlong_as_double((__double_as_longlong(f) & ~1LL) | (long long)sw);
+__host__ __device__ __forceinline__ double pack_flag(double f, int sw) {
+  return dfrom((dbits(f) & ~1LL) | (long long)sw);
 }
-__device__ __forceinline__ float pack_flag(float f, int sw) { return __int_as_float((__float_as_int(f) & ~1) | sw); }
-__device__ __forceinline__ int flag_of(double f) { return (int)(__double_as_longlong(f) & 1LL); }
-__device__ __forceinline__ int flag_of(float f) { return __float_as_int(f) & 1; }
+__host__ __device__ __forceinline__ float pack_flag(float f, int sw) { return ffrom((fbits(f) & ~1) | sw); }
+__host__ __device__ __forceinline__ int flag_of(double f) { return (int)(dbits(f) & 1LL); }
+__host__ __device__ __forceinline__ int flag_of(float f) { return fbits(f) & 1; }
 
 // Inverse iteration for the eigenvector of the tridiagonal (d, e) nearest
 // the shift sg: T - sg I = P L U is factored once by Gaussian elimination
@@ -180,7 +230,7 @@ __device__ __forceinline__ int flag_of(float f) { return __float_as_int(f) & 1; 
 // bit), 1 the reciprocal of the pivot u0, 2 the first superdiagonal u1 (the
 // second, u2, is e_{i+1} after an interchange and zero otherwise).
 template <typename T, typename TZ>
-__device__ void inv_iter(const T* __restrict__ d, const T* __restrict__ e, int p, T sg, TZ* __restrict__ z, size_t zs,
+__host__ __device__ void inv_iter(const T* __restrict__ d, const T* __restrict__ e, int p, T sg, TZ* __restrict__ z, size_t zs,
                          T* __restrict__ w, size_t ws, int q) {
   const T tiny = K<T>::eps;
   T a = d[0] - sg, bc = p > 1 ? e[0] : (T)0;

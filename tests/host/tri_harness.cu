@@ -1,0 +1,22 @@
+// Host build of the tridiagonal helpers of the Rayleigh-Ritz eigensolvers
+// (paper_1912_02767_gb300/csrc/tri_common.cuh), for CPU tests of their
+// arithmetic: the two Sturm counts and inverse iteration.  Test
+// infrastructure only; nothing here runs on a GPU.
+#include "../../paper_1912_02767_gb300/csrc/tri_common.cuh"
+
+using namespace sdpg::tri;
+
+extern "C" {
+// eigenvalues of the tridiagonal (d, e2 = e^2) below x, by the signs of the
+// leading principal minors
+int h_count_minors(const double* d, const double* e2, int p, double x) { return sturm_below_minors(d, e2, p, x); }
+// the same by the pivots of LDL^T (pivots below pivmin taken as -pivmin)
+int h_count_ratio(const double* d, const double* e2, int p, double x, double pivmin) {
+  return sturm_below(d, e2, p, x, pivmin);
+}
+// inverse iteration for the eigenvector nearest the shift sg; z (p) out,
+// w (3 p) scratch; q selects the start vector
+void h_inv_iter(const double* d, const double* e, int p, double sg, double* z, double* w, int q) {
+  inv_iter<double, double>(d, e, p, sg, z, 1, w, 1, q);
+}
+}
