@@ -4,7 +4,9 @@ signs of the leading principal minors and by the LDL^T pivots, against the
 eigenvalues numpy computes, including the cases random matrices never reach
 (a minor that is exactly zero, decoupled blocks, chains long enough to need
 rescaling); inverse iteration (one factorization, three solves) against
-numpy's eigenvectors, with and without row interchanges."""
+numpy's eigenvectors, with and without row interchanges.  Also the device
+Philox4x32-10 against the published known-answer vectors (the oracle's own
+Philox is pinned to the same vectors in test_oracle_eig.py)."""
 import ctypes as C
 import os
 import shutil
@@ -33,6 +35,9 @@ def lib():
     L.h_count_ratio.argtypes = [dp, dp, C.c_int, C.c_double, C.c_double]
     L.h_inv_iter.argtypes = [dp, dp, C.c_int, C.c_double, dp, dp, C.c_int]
     L.h_inv_iter.restype = None
+    up = C.POINTER(C.c_uint)
+    L.h_philox.argtypes = [up, C.c_uint, C.c_uint, up]
+    L.h_philox.restype = None
     return L
 
 
@@ -148,3 +153,15 @@ def test_inverse_iteration_finds_the_eigenvector(lib, kind):
     if kind == "interchanges":  # the interchange flag rides in the multipliers' last bit
         flags = [int(np.frombuffer(np.float64(v).tobytes(), dtype=np.int64)[0] & 1) for v in w[0::3][: p - 1]]
         assert 0 < sum(flags) < p - 1
+
+
+def test_device_philox_matches_the_known_answer_vectors(lib):
+    path = os.path.join(HERE, "golden", "philox4x32_10_kat.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert rows
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        ctr = (C.c_uint * 4)(*v[0:4])
+        out = (C.c_uint * 4)()
+        lib.h_philox(ctr, v[4], v[5], out)
+        assert list(out) == v[6:10], r
