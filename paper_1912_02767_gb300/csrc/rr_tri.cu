@@ -8,9 +8,10 @@
 //   G = L~ D L~^T           (Cholesky-QR in LDL^T form, L~ unit lower)
 //   H = D^{-1/2} L~^{-1} M L~^{-T} D^{-1/2}   (two unit-triangular solves)
 //   H = Q T Q^T             (Householder tridiagonalization)
-//   top `keep` eigenvalues of T by Sturm-sequence multisection, their
-//   eigenvectors by inverse iteration, orthonormalized (classical Gram-
-//   Schmidt, twice), back-transformed by Q
+//   top `keep` eigenvalues of T by Sturm-sequence multisection (FP32, then
+//   refined in FP64 by the division-free count of tri_common.cuh), their
+//   eigenvectors by inverse iteration, orthonormalized within clusters of
+//   close eigenvalues (classical Gram-Schmidt, twice), back-transformed by Q
 //   Coef = L~^{-T} D^{-1/2} Y  (S Coef = the Ritz vectors)
 // This is the textbook route for a few eigenpairs of a dense symmetric matrix
 // (Householder reduction, Wilkinson's bisection on the Sturm count, inverse

@@ -1,9 +1,14 @@
 // rr_wide.cu -- the Rayleigh-Ritz step of LOBPCG (Algorithm 3; as in
 // Algorithm 2) for one wide trial subspace spread over the whole GPU, by
-// tridiagonal reduction.  H = L^{-1} M L^{-T} comes from the cooperative
-// Cholesky factorisation and inverse (rr_large.cu) and two batched GEMM
-// launches; then
-//   k_trid_coop    Householder tridiagonalization of H in a working copy of
+// tridiagonal reduction.  H = L^{-1} M L^{-T} comes from the blocked
+// Cholesky factorisation and inverse with split products (rr_blocked.cu,
+// oz_gemm.cu; the FP64 path: the cooperative one of rr_large.cu) and two
+// products; then
+//   k_trid_cluster Householder tridiagonalization of H on one thread-block
+//                  cluster, H in its distributed shared memory (while it fits)
+//   k_latrd_coop   otherwise, blocked: panels of reflectors on every SM, the
+//                  rank-2k trailing updates as split products (mixed path)
+//   k_trid_coop    or unblocked (FP64 and FP32 paths): in a working copy of
 //                  precision T (L2-resident); column c belongs to CTA
 //                  c mod gridDim.x; two grid barriers per step; the tail
 //                  scales (d, e) to unit Gershgorin norm
@@ -13,8 +18,9 @@
 //   k_trid_shift   inverse-iteration shifts (sequential prefix)
 //   k_trid_invit   inverse iteration, one thread per eigenvector
 //   k_trid_backtr  Y = Q Z: every CTA applies all reflectors to its own
-//                  vectors (block-level reductions only)
-// and, by GEMM and cooperative-Cholesky launches, Cholesky-QR twice of Y and
+//                  vectors (block-level reductions only); the mixed path
+//                  uses the compact-WY form with split products instead
+// and, by products and Cholesky launches, Cholesky-QR twice of Y and
 // Coef = L^{-T} Y.
 //
 // Vector scratch (`vb`, T elements): d, e, e2, tau, w (p each), lam, sig
