@@ -88,3 +88,19 @@ def test_default_rayleigh_ritz_settings(lib):
     assert s.rr_method == 0 and s.rr_fp32 == 0 and s.precision == sdpgpu.PREC_FP64
     # Algorithm 3's full trial subspace span(X, R, dX) unless soft locking is asked for
     assert s.soft_lock == 0 and s.proj_neg == 0 and s.exact_solver == 0
+
+
+@pytest.mark.parametrize("field,value", [
+    ("rho", 0.0), ("sigma", -1.0), ("alpha", 2.0), ("eps_abs", -1e-4), ("max_iter", 0), ("check_every", 0),
+    ("lobpcg_max_iter", 0), ("precision", 3), ("rr_method", 2), ("rr_fp32", 2), ("proj_neg", 2),
+    ("exact_solver", 2), ("soft_lock", 2), ("tol_coef", 0.0), ("expand_frac", 0.0), ("mode_frac", 0.6)])
+def test_invalid_settings_are_refused_before_any_device_call(lib, field, value):
+    """sdp_create checks every setting before it touches the device: an out-of-
+    range value returns SDP_E_INVALID and creates nothing (no GPU needed)."""
+    import ctypes
+    from paper_1912_02767_gb300 import sdpgpu
+    s = sdpgpu.settings()
+    setattr(s, field, value)
+    h = ctypes.c_void_p()
+    rc = sdpgpu.load().sdp_create(ctypes.byref(h), ctypes.byref(s), None)
+    assert rc == -1 and not h.value, (field, value, rc)
