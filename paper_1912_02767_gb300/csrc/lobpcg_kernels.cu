@@ -290,9 +290,10 @@ __global__ void k_resid(Inst* insts, WorkMap wm) {
 }
 
 // Per instance: convergence test (every Ritz pair of the block within tol,
-// no fresh columns), residual summaries, and soft locking: only the
-// columns whose residual is above tol (fresh columns always) contribute
-// their R and Delta X to the next trial subspace [X, R_act, dX_act].
+// no fresh columns), residual summaries, and the columns whose R and
+// Delta X enter the next trial subspace [X, R_act, dX_act]: every column
+// with a nonzero residual (Algorithm 3), or with soft locking only those
+// still above tol (fresh columns always).
 // last_allowed = 0: the step budget is spent, stop.
 __global__ void k_resid_finish(Inst* insts, const int* list, int last_allowed) {
   const Inst& I = insts[list[blockIdx.x]];
