@@ -333,16 +333,25 @@ ORACLE_SAMPLE = [(256, 0.01), (256, 0.05), (256, 0.25), (1024, 0.01), (1024, 0.0
 
 
 def host_info():
-    """Host cores of this machine (the GPU machine's when run there)."""
-    model = None
+    """Host cores of this machine (the GPU machine's when run there) and its CPU:
+    the model name on x86; on Arm, where /proc/cpuinfo names no model, the
+    implementer and part codes."""
+    import platform
+    model, impl, part = None, None, None
     try:
         for ln in open("/proc/cpuinfo"):
-            if ln.lower().startswith(("model name", "cpu model")):
+            key = ln.split(":", 1)[0].strip().lower()
+            if key in ("model name", "cpu model") and model is None:
                 model = ln.split(":", 1)[1].strip()
-                break
+            elif key == "cpu implementer" and impl is None:
+                impl = ln.split(":", 1)[1].strip()
+            elif key == "cpu part" and part is None:
+                part = ln.split(":", 1)[1].strip()
     except OSError:
         pass
-    return {"host_cores": os.cpu_count(), "host_cpu": model}
+    if model is None and (impl or part):
+        model = "%s (cpu implementer %s, part %s)" % (platform.machine(), impl, part)
+    return {"host_cores": os.cpu_count(), "host_cpu": model or platform.machine() or None}
 
 
 def oracle_tol(m):
